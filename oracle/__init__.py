@@ -1,0 +1,179 @@
+"""CPU oracle for finite-source binary-lens magnification (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The GPU library never calls it, and it
+shares no code with the CUDA sources.
+
+The computation lives in ``twinkle_oracle.c`` (long double C99, OpenMP over
+source positions); this module compiles it in-tree on first use and wraps it
+with ctypes.  Every function states the part of the paper it follows in the C
+source; in short:
+
+* ``quintic``      -- polynomial of Eq. 1 by generic expansion (not Eq. 6)
+* ``images``       -- its roots, residuals (Eq. 12), Jacobians (Eq. 7), ghost pair test
+* ``mag``          -- magnification = image area / source area (Sec. 1), image
+                      area by a linking-free contour integral (Eq. 8)
+* ``crossings``    -- limb/caustic crossing angles, by the caustic or an image-count scan
+* ``caustic``      -- critical curve J = 0 and its caustic image
+* ``trajectory``   -- straight-line source trajectory of a light curve
+* ``rayshoot``     -- brute-force inverse ray shooting (Sec. 1), for pinning ``mag``
+
+Per-position status codes from ``mag``: 0 ok, 1 crossing detectors disagree or
+image counts are inconsistent, 2 quadrature did not converge, 3 root finder
+failure, 4 invalid input.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "twinkle_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS_OK, STATUS_XING, STATUS_QUAD, STATUS_ROOT, STATUS_INPUT = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library in-tree (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC]
+        if platform.machine() in ("x86_64", "AMD64", "i686"):
+            cmd.append("-lquadmath")  # binary128 working type on x86 (see the C source)
+        cmd.append("-lm")
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_SO)
+        d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+        P = ctypes.c_void_p
+        lib.orc_quintic.argtypes = [d, d, d, d, P]
+        lib.orc_quintic.restype = None
+        lib.orc_images.argtypes = [d, d, d, d, P, P, P, P, P]
+        lib.orc_images.restype = ctypes.c_int
+        lib.orc_caustic.argtypes = [d, d, ctypes.c_int, P, P]
+        lib.orc_caustic.restype = ctypes.c_int
+        lib.orc_crossings.argtypes = [d, d, d, d, d, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
+        lib.orc_crossings.restype = ctypes.c_int
+        lib.orc_mag.argtypes = [d, d, d, P, P, i64, ctypes.c_int, ctypes.c_int, P, P, P]
+        lib.orc_mag.restype = ctypes.c_int
+        lib.orc_trajectory.argtypes = [d, d, d, d, P, i64, P, P]
+        lib.orc_trajectory.restype = None
+        lib.orc_rayshoot.argtypes = [d, d, d, d, d, d, d, d, d, i64, i64, ctypes.c_int]
+        lib.orc_rayshoot.restype = d
+        lib.orc_real_bits.argtypes = []
+        lib.orc_real_bits.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def real_bits() -> int:
+    """Mantissa bits of the oracle's working type (113: IEEE binary128)."""
+    return _load().orc_real_bits()
+
+
+def quintic(s: float, q: float, zeta: complex) -> np.ndarray:
+    """Ascending coefficients c0..c5 of the image polynomial (centre-of-mass frame)."""
+    out = np.zeros(12)
+    _load().orc_quintic(s, q, zeta.real, zeta.imag, _ptr(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def images(s: float, q: float, zeta: complex) -> dict:
+    """Roots, residuals, Jacobians, real mask and image count of one point source."""
+    roots, res, jac = np.zeros(10), np.zeros(10), np.zeros(5)
+    isreal = np.zeros(5, np.int32)
+    count = np.zeros(1, np.int32)
+    st = _load().orc_images(s, q, zeta.real, zeta.imag, _ptr(roots), _ptr(res), _ptr(jac), _ptr(isreal), _ptr(count))
+    if st:
+        raise RuntimeError("oracle root finder failed (status %d)" % st)
+    return dict(
+        roots=roots[0::2] + 1j * roots[1::2],
+        residuals=res[0::2] + 1j * res[1::2],
+        jac=jac,
+        real=isreal.astype(bool),
+        count=int(count[0]),
+    )
+
+
+def caustic(s: float, q: float, M: int = 1024):
+    """Critical curve and caustic at M angles: two complex arrays of shape (M, 4)."""
+    zc, cc = np.zeros(8 * M), np.zeros(8 * M)
+    st = _load().orc_caustic(s, q, M, _ptr(zc), _ptr(cc))
+    if st:
+        raise RuntimeError("oracle caustic failed")
+    return (zc[0::2] + 1j * zc[1::2]).reshape(M, 4), (cc[0::2] + 1j * cc[1::2]).reshape(M, 4)
+
+
+def crossings(s: float, q: float, rho: float, y1: float, y2: float, method: str = "caustic", K: int = 4096) -> np.ndarray:
+    """Limb angles where the source limb crosses the caustic.
+
+    method="caustic": limb/caustic intersections (caustic sampled at K angles);
+    method="scan": changes of the image count on K limb points.
+    """
+    out = np.zeros(64)
+    m = 1 if method == "caustic" else 2
+    n = _load().orc_crossings(s, q, rho, y1, y2, m, K, _ptr(out), 64)
+    if n < 0:
+        raise RuntimeError("oracle crossings failed")
+    return np.sort(out[: min(n, 64)])
+
+
+def mag(s: float, q: float, rho: float, y1, y2, scan_K: int = 256, nthreads: int = 0):
+    """Finite-source magnifications of positions (y1[i], y2[i]).
+
+    Returns (mu, status, nxing) arrays.  ``scan_K`` > 0 cross-checks the caustic
+    crossings by an image-count scan on that many limb points.
+    """
+    y1 = np.ascontiguousarray(np.atleast_1d(y1), dtype=np.float64)
+    y2 = np.ascontiguousarray(np.atleast_1d(y2), dtype=np.float64)
+    n = y1.size
+    out = np.zeros(n)
+    st = np.zeros(n, np.int32)
+    nx = np.zeros(n, np.int32)
+    rc = _load().orc_mag(s, q, rho, _ptr(y1), _ptr(y2), n, scan_K, nthreads, _ptr(out), _ptr(st), _ptr(nx))
+    if rc:
+        raise ValueError("oracle: invalid lens or source parameters")
+    return out, st, nx
+
+
+def trajectory(u0: float, alpha: float, t0: float, tE: float, times):
+    """Source positions along a straight-line trajectory."""
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    y1, y2 = np.zeros(t.size), np.zeros(t.size)
+    _load().orc_trajectory(u0, alpha, t0, tE, _ptr(t), t.size, _ptr(y1), _ptr(y2))
+    return y1, y2
+
+
+def lightcurve(s, q, rho, u0, alpha, t0, tE, times, scan_K: int = 256, nthreads: int = 0):
+    """Magnification along a straight-line trajectory."""
+    y1, y2 = trajectory(u0, alpha, t0, tE, times)
+    return mag(s, q, rho, y1, y2, scan_K=scan_K, nthreads=nthreads)
+
+
+def rayshoot(s, q, rho, y1, y2, box, npix: int, nthreads: int = 0) -> float:
+    """Brute-force inverse ray shooting over box=(x0, x1, y0, y1) with npix x npix rays."""
+    x0, x1, yb0, yb1 = box
+    return _load().orc_rayshoot(s, q, rho, y1, y2, x0, x1, yb0, yb1, npix, npix, nthreads)

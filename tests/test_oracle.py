@@ -1,0 +1,222 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: an
+independent formula printed in the paper (Eq. 6), closed forms of the
+single-lens limit, algebraic invariants of the binary-lens polynomial
+(Sec. 2.3-2.4), symmetries of the lens, brute-force inverse ray shooting
+(Sec. 1), and the agreement of two independent caustic-crossing detectors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def eq6_planet_frame(s, q, y):
+    """Coefficients c0..c5 of Eq. 6 (paper Sec. 2.2), origin at the secondary.
+
+    Readings: the factor printed as "Im(y) i" is i*Im(y); m1 = 1 - m2."""
+    m2 = q / (1 + q)
+    yb = np.conj(y)
+    vc = yb + s
+    vp = 1 + s * yb
+    iim = 1j * y.imag
+    c5 = -yb * vc
+    c4 = (yb * y - 1 - 2 * s * yb) * vc + m2 * s
+    c3 = (2 * y - s) * (vp * vc + 2 * iim - m2 * s) + 4 * (m2 * s - y) * iim
+    c2 = (vp.real ** 2 * vc.real + 1j * y.imag * vp.real * (1 - s * y).real + s * y.imag ** 2 * (2 + s * vc)
+          + m2 * s * (2 * yb * (y - s) - (1 - s * y)))
+    c1 = m2 * s * ((s + 2 * y) * vp + s * (2 * s * iim - m2))
+    c0 = s * s * m2 * m2 * y
+    return np.array([c0, c1, c2, c3, c4, c5])
+
+
+def taylor_shift(c, a):
+    """Coefficients of P(x + a) from those of P(x) (ascending)."""
+    n = len(c)
+    out = np.zeros(n, complex)
+    for k in range(n):
+        for j in range(k + 1):
+            out[j] += c[k] * math.comb(k, j) * a ** (k - j)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_generic_quintic_equals_eq6(seed):
+    """The oracle's generically expanded polynomial is the paper's Eq. 6 (after
+    moving the origin from the centre of mass to the secondary)."""
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        s = 10 ** rng.uniform(-0.5, 0.5)
+        q = 10 ** rng.uniform(-3, 0)
+        zeta = complex(rng.uniform(-1.5, 1.5), rng.uniform(-1.5, 1.5))
+        z2 = s / (1 + q)
+        c_cm = O.quintic(s, q, zeta)
+        c_pl = taylor_shift(c_cm, z2)  # P(eta + z2)
+        e6 = eq6_planet_frame(s, q, zeta - z2)
+        r = c_pl / c_pl[5] * e6[5]
+        assert np.max(np.abs(r - e6)) <= 1e-11 * np.max(np.abs(e6))
+
+
+def test_roots_vieta_and_residual_sum():
+    """Roots satisfy Vieta's sum rule, and the lens-equation residuals of the
+    five roots sum to zero (Eq. 13-14); real images number 3 or 5 with parity
+    sum -1 (Sec. 2.3); ghosts come as a pair of opposite residuals (Sec. 2.4.1)."""
+    rng = np.random.default_rng(7)
+    n3 = n5 = 0
+    for k in range(300):
+        if k % 2:  # wide lenses, sources anywhere
+            s = 10 ** rng.uniform(-0.5, 0.5)
+            q = 10 ** rng.uniform(-6, 0)
+            zeta = complex(rng.uniform(-1, 1), rng.uniform(-0.6, 0.6))
+        else:  # resonant lenses, sources near the large central caustic
+            s = 10 ** rng.uniform(-0.1, 0.1)
+            q = 10 ** rng.uniform(-1, 0)
+            zeta = complex(rng.uniform(-0.15, 0.15), rng.uniform(-0.15, 0.15))
+        c = O.quintic(s, q, zeta)
+        im = O.images(s, q, zeta)
+        r, R = im["roots"], im["residuals"]
+        assert abs(r.sum() + c[4] / c[5]) <= 1e-9 * (1 + np.abs(r).max())
+        assert abs(R.sum()) <= 1e-9
+        assert im["count"] in (3, 5)
+        real = im["real"]
+        assert real.sum() == im["count"]
+        par = np.sign(im["jac"][real])
+        assert par.sum() == -1
+        if im["count"] == 3:
+            g = R[~real]
+            assert abs(g[0] + g[1]) < 1e-6 * abs(g[0])
+            assert np.abs(R[real]).max() < 1e-12
+            n3 += 1
+        else:
+            n5 += 1
+    assert n3 > 50 and n5 > 10
+
+
+def test_image_count_matches_caustic_inside_outside():
+    """Five images inside the caustic, three outside (Sec. 2.3): for X2's lens
+    the centre of the central caustic has 5 images, a far point 3."""
+    assert O.images(1.0, 0.1, complex(0.0, 0.0))["count"] == 5
+    assert O.images(1.0, 0.1, complex(1.5, 1.0))["count"] == 3
+
+
+@pytest.mark.parametrize("rho", [1.0, 0.1, 0.01])
+def test_centred_disc_point_lens(rho):
+    """Uniform disc centred on a point lens: image is an annulus, mu = sqrt(1 + 4/rho^2).
+
+    The binary is made a point lens by a negligible companion far away
+    (q = 1e-9 at s = 10); its effect on mu is ~1e-9."""
+    s, q = 10.0, 1e-9
+    x1 = -q * s / (1 + q)
+    mu, st, _ = O.mag(s, q, rho, [x1], [0.0], scan_K=64)
+    assert st[0] == 0
+    assert abs(mu[0] / math.sqrt(1 + 4 / rho ** 2) - 1) < 3e-9
+
+
+@pytest.mark.parametrize("u", [0.1, 0.5, 1.0])
+def test_paczynski_limit(u):
+    """rho -> 0 and q -> 0: mu -> (u^2 + 2)/(u sqrt(u^2 + 4)); the leading
+    finite-source correction is O(rho^2/u^2)."""
+    s, q, rho = 10.0, 1e-9, 1e-5
+    x1 = -q * s / (1 + q)
+    mu, st, _ = O.mag(s, q, rho, [x1 + u], [0.0], scan_K=64)
+    A = (u * u + 2) / (u * math.sqrt(u * u + 4))
+    assert st[0] == 0
+    assert abs(mu[0] / A - 1) < 2e-9 + rho ** 2 / u ** 2
+
+
+def single_lens_polygon(u, rho, n):
+    """Area of the images of a disc under a unit point lens, by the polygon of
+    the analytic images z = zeta/2 (1 +- sqrt(1 + 4/|zeta|^2)) of n limb
+    points, each image weighted by its parity (+1 outer, -1 inner)."""
+    th = 2 * np.pi * np.arange(n) / n
+    zeta = u + rho * np.exp(1j * th)
+    root = np.sqrt(1 + 4 / np.abs(zeta) ** 2)
+    area = 0.0
+    for sgn in (+1, -1):
+        z = zeta / 2 * (1 + sgn * root)
+        zn = np.roll(z, -1)
+        area += sgn * 0.5 * np.sum(z.real * zn.imag - z.imag * zn.real)
+    return area / (np.pi * rho * rho)
+
+
+@pytest.mark.parametrize("u,rho", [(0.05, 0.1), (0.3, 0.1), (1.5, 0.4), (0.02, 0.01)])
+def test_single_lens_finite_source(u, rho):
+    """Finite-source single-lens magnification at any u: a periodic 1-D integral
+    over the analytic images (Richardson-extrapolated polygon)."""
+    n = 1 << 16
+    ref = (4 * single_lens_polygon(u, rho, 2 * n) - single_lens_polygon(u, rho, n)) / 3
+    s, q = 10.0, 1e-9
+    x1 = -q * s / (1 + q)
+    mu, st, _ = O.mag(s, q, rho, [x1 + u], [0.0], scan_K=64)
+    assert st[0] == 0
+    assert abs(mu[0] / ref - 1) < 5e-8
+
+
+def test_symmetries():
+    """Mirror about the lens axis, mu(y1, y2) = mu(y1, -y2); and mass swap,
+    mu(s, q, y1, y2) = mu(s, 1/q, -y1, y2) (swapping the masses of Eq. 2
+    reflects the lens through the centre of mass)."""
+    s, q, rho = 1.0, 0.1, 0.05
+    y1 = np.array([0.05, -0.1, 0.3])
+    y2 = np.array([0.02, 0.1, -0.05])
+    a, sa, _ = O.mag(s, q, rho, y1, y2, scan_K=64)
+    b, sb, _ = O.mag(s, q, rho, y1, -y2, scan_K=64)
+    c, sc, _ = O.mag(s, 1 / q, rho, -y1, y2, scan_K=64)
+    assert (sa == 0).all() and (sb == 0).all() and (sc == 0).all()
+    np.testing.assert_allclose(a, b, rtol=1e-10)
+    np.testing.assert_allclose(a, c, rtol=1e-10)
+
+
+def test_magnification_at_least_one_and_large_source_limit():
+    """mu >= 1 for a lens of non-negative point masses; mu -> 1 as rho grows
+    (a source much larger than the Einstein ring)."""
+    rng = np.random.default_rng(3)
+    y1 = rng.uniform(-1, 1, 12)
+    y2 = rng.uniform(-1, 1, 12)
+    mu, st, _ = O.mag(0.8, 0.3, 0.02, y1, y2, scan_K=32)
+    assert (st == 0).all()
+    assert (mu >= 1).all()
+    big = O.mag(0.8, 0.3, 50.0, [0.0, 3.0], [0.0, -2.0], scan_K=32)[0]
+    assert (big > 1).all() and (big < 1.002).all()
+
+
+@pytest.mark.parametrize(
+    "s,q,rho,y1,y2",
+    [
+        (1.0, 0.1, 0.1, 0.2, 0.2),  # Fig. 2 configuration: two caustic crossings
+        (1.0, 0.5, 0.05, 0.0, 0.0),  # source inside the central caustic: 5 images
+        (1.0, 0.5, 0.05, 0.12, 0.1),  # limb across a fold
+        (0.8, 1e-2, 0.02, -0.3, 0.05),
+    ],
+)
+def test_brute_force_ray_shooting(s, q, rho, y1, y2):
+    """Inverse ray shooting on a fine image-plane grid (Sec. 1) agrees with the
+    contour integral to its own resolution."""
+    mu, st, _ = O.mag(s, q, rho, [y1], [y2], scan_K=128)
+    ray = O.rayshoot(s, q, rho, y1, y2, (-2.2, 2.2, -2.2, 2.2), 8000)
+    assert st[0] == 0
+    assert abs(mu[0] / ray - 1) < 1.5e-3
+
+
+def test_crossing_detectors_agree():
+    """Limb/caustic intersections and the image-count scan find the same angles."""
+    cases = [(1.0, 0.1, 0.1, 0.2, 0.2), (1.0, 1e-3, 1e-3, 0.0, 0.0), (0.8, 1e-4, 5e-4, -0.45, 0.0175)]
+    for s, q, rho, y1, y2 in cases:
+        a = O.crossings(s, q, rho, y1, y2, "caustic", 2048)
+        b = O.crossings(s, q, rho, y1, y2, "scan", 1024)
+        assert len(a) == len(b) and len(a) % 2 == 0
+        assert np.max(np.abs(a - b), initial=0) < 1e-9
+
+
+def test_trajectory_geometry():
+    """Straight-line trajectory: closest approach |u0| at t0, direction alpha."""
+    u0, alpha, t0, tE = 0.01, 1.0, 3.0, 20.0
+    t = np.array([t0 - tE, t0, t0 + tE])
+    y1, y2 = O.trajectory(u0, alpha, t0, tE, t)
+    assert abs(math.hypot(y1[1], y2[1]) - abs(u0)) < 1e-15
+    d = np.array([y1[2] - y1[1], y2[2] - y2[1]])
+    assert abs(math.atan2(d[1], d[0]) - alpha) < 1e-14
+    assert abs(np.hypot(*d) - 1) < 1e-14
