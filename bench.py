@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Throughput benchmark: finite-source magnifications per second on GB300.
+
+One step = one call of the C ABI over the whole workload (every position
+integrated to rel_tol), inputs resident in device memory.  Default workload:
+the 512 x 512 planetary-caustic magnification map (s=0.8, q=1e-4, rho=5e-4,
+rel_tol=1e-4), FP64 mode.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--mode fp64|mixed]
+    python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Multi-GPU (torchrun, one rank per GPU): every rank integrates its own copy of
+the workload (independent positions: weak scaling, no collective on the data
+path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# ---------------------------------------------------------------- FLOP model
+# Algorithmic FLOPs of the method per unit of work counted by the kernel
+# (tw_last_launch_work).  Counting rules: real add/mul 1, complex add 2,
+# complex mul 6, complex multiply-add 8, reciprocal/division/sqrt 1.
+#   one Aberth sweep (five roots): per root Horner p and p' (5 x 16), p/p' (12),
+#     sum of four reciprocal differences (38), correction (22): 152 -> 760
+#   one limb sample outside the sweeps: limb point (8), Eq. 6 coefficients
+#     (~100), residual/Jacobian/f'/f'' per root (68 -> 340), dz/dtheta and
+#     z' ^ z'' per root (29 -> 145): ~600 (FP64)
+#   mixed mode adds one FP64 Newton step per root per sample (5 x 94 = 470)
+#   one edge: image linking distances and 3-5 links of trapezium + parabolic
+#     correction + four error terms: ~145 (FP64), ~20 (FP32)
+F_SWEEP = 760.0
+F_SAMPLE64 = 600.0
+F_NEWTON64 = 470.0
+F_EDGE64 = 145.0
+F_EDGE32 = 20.0
+# Peaks (FLOP/s).  FP64: GB300's nominal FP64 rate (1.25 TFLOP/s); FP32: 152 SMs
+# x 128 FP32 lanes x 2 FLOP/FMA x 2.07 GHz maximum SM clock.
+PEAK_FP64 = 1.25e12
+PEAK_FP32 = 152 * 128 * 2 * 2.07e9
+
+
+def workload(name):
+    from paper_2501_03322_gb300 import workloads as W
+
+    if name == "map_planetary":
+        c = W.MAP_PLANETARY
+        y1, y2 = W.map_grid()
+        return dict(kind="mag", name="map_planetary_512x512", s=c["s"], q=c["q"], rho=c["rho"], y1=y1, y2=y2,
+                    rel_tol=c["rel_tol"], n=y1.size)
+    if name == "lightcurve_central":
+        c = W.LIGHTCURVE_CENTRAL
+        t = W.lightcurve_central_times(c["n"])
+        return dict(kind="lc", name="lightcurve_central_1000", times=t, n=t.size, **{k: c[k] for k in
+                    ("s", "q", "rho", "u0", "alpha", "t0", "tE", "rel_tol")})
+    if name == "stress_resonant":
+        c = W.STRESS_RESONANT
+        y1, y2 = W.stress_positions()
+        return dict(kind="mag", name="stress_resonant_1e6", s=c["s"], q=c["q"], rho=c["rho"], y1=y1, y2=y2,
+                    rel_tol=c["rel_tol"], n=y1.size)
+    if name == "batch_lightcurves":
+        params, offsets, times = W.batch_lightcurves()
+        return dict(kind="batch", name="batch_lightcurves_4096", params=params, offsets=offsets, times=times,
+                    rel_tol=W.BATCH_LIGHTCURVES["rel_tol"], n=times.size)
+    raise SystemExit("unknown workload " + name)
+
+
+def config_of(wl, mode, n_gpus):
+    cfg = {"workload": wl["name"], "positions_per_gpu": int(wl["n"]), "rel_tol": wl["rel_tol"], "mode": mode,
+           "parallelism": "dp%d" % n_gpus, "l2": "flushed between timed steps (256 MiB write)"}
+    for k in ("s", "q", "rho"):
+        if k in wl:
+            cfg[k] = wl[k]
+    return cfg
+
+
+def sources_sha():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2501_03322_gb300", "csrc")
+    for fn in sorted(os.listdir(cs)):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(cs, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(wl_name, mode):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    from the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "contour_%s_%s.md" % (mode, wl_name))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if "=" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split("=", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != sources_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_scaled"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flops_of(work, mode):
+    f64 = (F_SAMPLE64 * work["samples"] + F_SWEEP * work["sweeps64"] + F_EDGE64 * work["edges"])
+    if mode == "mixed":
+        f64 += F_NEWTON64 * work["samples"]
+    f32 = F_SWEEP * work["sweeps32"] + F_EDGE32 * work["edges"]
+    return f64, f32
+
+
+def cpu_oracle_sample(wl, k, seed=777):
+    """Time the CPU oracle on k positions of the workload using every host core."""
+    import oracle as O
+    from paper_2501_03322_gb300 import workloads as W
+
+    idx = W.sample_indices(int(wl["n"]), k, seed=seed)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    if wl["kind"] == "mag":
+        O.mag(wl["s"], wl["q"], wl["rho"], wl["y1"][idx], wl["y2"][idx], nthreads=cores)
+    elif wl["kind"] == "lc":
+        O.lightcurve(wl["s"], wl["q"], wl["rho"], wl["u0"], wl["alpha"], wl["t0"], wl["tE"], wl["times"][idx],
+                     nthreads=cores)
+    else:
+        offs = wl["offsets"]
+        curve = np.searchsorted(offs, idx, side="right") - 1
+        for k_c in np.unique(curve):
+            s, q, rho, u0, al, t0_, tE = wl["params"][k_c]
+            O.lightcurve(s, q, rho, u0, al, t0_, tE, wl["times"][idx[curve == k_c]], nthreads=cores)
+    dt = time.perf_counter() - t0
+    return len(idx), dt, cores
+
+
+def run_reference(args, wl, cfg, metric, unit):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    k = args.ref_sample
+    times = []
+    for i in range(args.warmup + args.steps):
+        n, dt, cores = cpu_oracle_sample(wl, k, seed=1000 + i)
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = k * len(times) / tot
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "binary128",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": "%d positions of the workload per step (seeded), all host cores" % k},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="map_planetary",
+                    choices=["map_planetary", "lightcurve_central", "stress_resonant", "batch_lightcurves"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cpu-sample", type=int, default=128, help="positions in the CPU oracle baseline sample")
+    ap.add_argument("--ref-sample", type=int, default=24, help="positions per step of the reference arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    metric = "finite-source mags/sec at rel.err<=1e-4: surrogate+fallback vs plain, 1 GB300"
+    unit = "mags/s"
+    wl = workload(args.workload)
+    cfg = config_of(wl, args.mode, args.gpus)
+    if args.impl == "reference":
+        run_reference(args, wl, cfg, metric, unit)
+        return
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2501_03322_gb300 as P
+
+    prec = P.PREC_FP64 if args.mode == "fp64" else P.PREC_MIXED
+    stream = torch.cuda.current_stream(dev)
+
+    def D(a, dt=torch.float64):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+
+    if wl["kind"] == "mag":
+        y1d, y2d = D(wl["y1"]), D(wl["y2"])
+        outd = torch.empty_like(y1d)
+
+        def step():
+            P.mag(wl["s"], wl["q"], wl["rho"], y1d, y2d, rel_tol=wl["rel_tol"], precision=prec, out=outd)
+    elif wl["kind"] == "lc":
+        td = D(wl["times"])
+        outd = torch.empty_like(td)
+
+        def step():
+            P.lightcurve(wl["s"], wl["q"], wl["rho"], wl["u0"], wl["alpha"], wl["t0"], wl["tE"], td,
+                         rel_tol=wl["rel_tol"], precision=prec, out=outd)
+    else:
+        pd, od, td = D(wl["params"]), D(wl["offsets"], torch.int64), D(wl["times"])
+        outd = torch.empty_like(td)
+
+        def step():
+            P.lightcurve_batch(pd, od, td, rel_tol=wl["rel_tol"], precision=prec, out=outd)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    f64 = f32 = 0.0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+        evs[i][1].synchronize()
+        w = P.last_launch_work()
+        a, b = flops_of(w, args.mode)
+        f64 += a
+        f32 += b
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    ms = [s.elapsed_time(e) for s, e in evs]
+    t_step = sum(ms) / len(ms) / 1e3
+    if dist:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+        dist.barrier()
+    value = world * wl["n"] / t_step
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    if wl["kind"] == "mag":
+        hy1 = torch.from_numpy(np.ascontiguousarray(wl["y1"])).pin_memory()
+        hy2 = torch.from_numpy(np.ascontiguousarray(wl["y2"])).pin_memory()
+        hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()
+        h2d, d2h = 16 * wl["n"], 9 * wl["n"]
+
+        def e2e_step():
+            P.mag(wl["s"], wl["q"], wl["rho"], hy1.numpy(), hy2.numpy(), rel_tol=wl["rel_tol"], precision=prec,
+                  out=hout.numpy())
+    elif wl["kind"] == "lc":
+        ht = torch.from_numpy(np.ascontiguousarray(wl["times"])).pin_memory()
+        hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()
+        h2d, d2h = 8 * wl["n"], 9 * wl["n"]
+
+        def e2e_step():
+            P.lightcurve(wl["s"], wl["q"], wl["rho"], wl["u0"], wl["alpha"], wl["t0"], wl["tE"], ht.numpy(),
+                         rel_tol=wl["rel_tol"], precision=prec, out=hout.numpy())
+    else:
+        hp = torch.from_numpy(wl["params"]).pin_memory()
+        ho = torch.from_numpy(wl["offsets"]).pin_memory()
+        ht = torch.from_numpy(wl["times"]).pin_memory()
+        hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()
+        h2d = 8 * (wl["params"].size + wl["offsets"].size + wl["times"].size)
+        d2h = 9 * wl["n"]
+
+        def e2e_step():
+            P.lightcurve_batch(hp.numpy(), ho.numpy(), ht.numpy(), rel_tol=wl["rel_tol"], precision=prec,
+                               out=hout.numpy())
+    e2e_step()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    n_e2e = max(2, args.steps // 2)
+    for _ in range(n_e2e):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e2e_step()
+    t_e2e = (time.perf_counter() - t0) / n_e2e
+    if dist:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+
+    # roofline of the contour kernel (the only kernel of a step)
+    f64 /= args.steps
+    f32 /= args.steps
+    t_roof = max(f64 / PEAK_FP64, f32 / PEAK_FP32)
+    roof = {"bound": "alu", "achieved": f64 / t_step / 1e12, "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
+            "frac": t_roof / t_step, "traffic": profile_traffic(args.workload, args.mode),
+            "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); FP32 side 152x128x2x2.07 GHz",
+            "fp64_flop_per_launch": f64, "fp32_flop_per_launch": f32,
+            "fp32_frac": (f32 / PEAK_FP32) / t_step}
+
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f32+f64", "data": "synthetic",
+            "config": cfg, "roofline": roof, "clocks": clocks,
+            "e2e": {"value": world * wl["n"] / t_e2e, "unit": unit, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps, "wall_s_timed": wall}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt, cores = cpu_oracle_sample(wl, args.cpu_sample)
+        line["cpu_baseline"] = {"value": n / dt, "unit": unit, "cores": cores, "kind": "oracle",
+                                "sample": "%d seeded positions of the same workload, %.1f s" % (n, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,139 @@
+/*
+ * twinkle.h -- C ABI of the GB300 finite-source binary-lens magnification
+ * library (libtwinkle_gb300.so).
+ *
+ * The problem (paper Sec. 2.1, Eq. 1-2; Sec. 2.3): a binary lens of total mass
+ * 1 with mass ratio q = m2/m1 > 0 and projected separation s > 0, in units of
+ * the angular Einstein radius (Eq. 3), with the origin at the centre of mass:
+ * the primary m1 = 1/(1+q) sits at x = -q s/(1+q), the secondary m2 = q/(1+q)
+ * at x = +s/(1+q), both on the real axis.  A uniform disc source of radius
+ * rho > 0 centred at zeta0 = y1 + i y2 is magnified by
+ *
+ *     mu = (total area of its images) / (pi rho^2)          (Sec. 1)
+ *
+ * which the library computes by contour integration of the images of the
+ * source limb (Sec. 2.3-2.5): cancellation-free quintic coefficients (Eq. 6),
+ * roots, ghost rejection by the lens-equation residual (Eq. 12-15), linking of
+ * real images by parity (Eq. 7), Green's-theorem area with parabolic and
+ * cross-caustic corrections (Eq. 8-11), error estimates (Eq. 17-18) and
+ * adaptive inverse-transform resampling of the limb until the estimated error
+ * is at most rel_tol * mu, or the sample cap is reached (Sec. 3).
+ *
+ * Memory: every pointer argument is owned by the caller and may point to host
+ * memory (pageable or pinned) or to device memory of the current CUDA device;
+ * the kind is detected per pointer.  All array arguments of one call must be
+ * of the same kind.  With host pointers the call is synchronous: inputs are
+ * copied to the device and outputs back before it returns.  With device
+ * pointers the call is asynchronous on opts->stream (NULL = the legacy default
+ * stream) and outputs are valid once that stream reaches the call; buffers
+ * must stay valid until then.  The library keeps its own device working
+ * memory (sample arenas, staging buffers) for the lifetime of the process; it
+ * never frees or retains caller memory.
+ *
+ * Errors: a negative return code means nothing was written (argument errors
+ * are detected before any device work).  TW_OK means every output element was
+ * written; per-position outcomes are reported in opts->pos_status when given.
+ * A positive return (warning) is only produced by synchronous (host-pointer)
+ * calls, after all outputs were written.
+ */
+#ifndef TWINKLE_GB300_H
+#define TWINKLE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+enum {
+    TW_OK = 0,
+    TW_EINVAL = -1,   /* invalid argument: n < 0, NULL with n > 0, non-finite or
+                         non-positive s, q, rho, tE or rel_tol, mixed pointer
+                         kinds, options out of range; nothing written */
+    TW_ECUDA = -2,    /* a CUDA runtime call failed (no device, launch error) */
+    TW_ENOMEM = -3,   /* device working memory could not be allocated */
+    TW_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    TW_WCAP = 1       /* synchronous call: >= 1 position reached the sample cap;
+                         its output holds the best estimate */
+};
+
+/* Per-position status bits written to tw_opts.pos_status. */
+enum {
+    TW_POS_OK = 0,
+    TW_POS_CAP = 1,        /* sample cap reached: mu is the estimate with the cap's
+                              samples, err_out its error estimate (Sec. 3) */
+    TW_POS_IMAGECOUNT = 2, /* a limb sample had no image set with 3 or 5 real
+                              images and parity sum -1 (Sec. 2.3) */
+    TW_POS_NONFINITE = 4,  /* non-finite input position or result (out is NaN) */
+    TW_POS_SOLVER = 8      /* root iteration stopped at its iteration limit */
+};
+
+/* Arithmetic modes. */
+enum {
+    TW_PREC_FP64 = 0, /* every step in FP64 */
+    TW_PREC_MIXED = 1 /* root iterations in FP32, then FP64 polish; coefficients
+                         (Eq. 6), residual test (Eq. 12) and area sums in FP64 */
+};
+
+typedef struct tw_opts {
+    int precision;        /* TW_PREC_FP64 (default) or TW_PREC_MIXED */
+    int samples_per_iter; /* limb samples added per iteration and initial sample
+                             count: 32, 64 (default, Sec. 3) or 128 */
+    int max_samples;      /* sample cap per position, 64..16384 (default 4096, Sec. 3) */
+    int autotune;         /* 1: choose the launch shape by timing a calibration
+                             subsample, cached per (GPU, mode, tolerance) */
+    void *stream;         /* cudaStream_t for device-pointer calls, or NULL */
+    double *err_out;      /* optional [n]: error estimate of mu (absolute) */
+    int32_t *nsamp_out;   /* optional [n]: limb samples used */
+    int8_t *pos_status;   /* optional [n]: TW_POS_* bits */
+} tw_opts;
+
+/* Fills *opts with the defaults listed above (all output pointers NULL). */
+void tw_opts_default(tw_opts *opts);
+
+/* Finite-source magnification of n source positions (y1[i], y2[i]) behind
+ * one binary lens (s, q) for one source radius rho; out[i] receives mu.
+ * rel_tol is the target relative error of mu (the paper's tolerance, Sec. 4.1).
+ * Layout: y1, y2, out are contiguous float64 arrays of n elements. */
+int tw_mag(double s, double q, double rho, const double *y1, const double *y2, int64_t n,
+           double rel_tol, double *out);
+int tw_mag_ex(double s, double q, double rho, const double *y1, const double *y2, int64_t n,
+              double rel_tol, double *out, const tw_opts *opts);
+
+/* Light curve: magnification at n times of a source moving on a straight
+ * line (the paper leaves the convention open; this library uses, with
+ * tau = (t - t0)/tE,  y1 = tau cos(alpha) - u0 sin(alpha),
+ * y2 = tau sin(alpha) + u0 cos(alpha), in the centre-of-mass frame).
+ * times and out are contiguous float64 arrays of n elements; tE > 0. */
+int tw_lightcurve(double s, double q, double rho, double u0, double alpha, double t0, double tE,
+                  const double *times, int64_t n, double rel_tol, double *out);
+int tw_lightcurve_ex(double s, double q, double rho, double u0, double alpha, double t0, double tE,
+                     const double *times, int64_t n, double rel_tol, double *out, const tw_opts *opts);
+
+/* Many light curves of uneven length in one persistent, work-stealing launch.
+ * params: [ncurve][7] float64 rows (s, q, rho, u0, alpha, t0, tE);
+ * offsets: [ncurve + 1] int64, offsets[0] = 0, non-decreasing; curve k owns
+ * times[offsets[k] .. offsets[k+1]) and the same range of out (and of the
+ * optional per-position outputs).  Total positions = offsets[ncurve]. */
+int tw_lightcurve_batch(const double *params, const int64_t *offsets, const double *times,
+                        int64_t ncurve, double rel_tol, double *out, const tw_opts *opts);
+
+/* Text of a return code (TW_OK, TW_E*, TW_WCAP). */
+const char *tw_status_str(int code);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int tw_version(void);
+
+/* Work done by the most recent launch on the current device (waits for it):
+ * out[0] limb samples, out[1] FP64 Aberth sweeps (five roots each), out[2]
+ * FP32 Aberth sweeps, out[3] edge evaluations (image linking + area + error).
+ * These are the units of the FLOP accounting of the roofline report; the
+ * paper has no counterpart (it reports no operation counts). */
+int tw_last_launch_work(int64_t out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TWINKLE_GB300_H */

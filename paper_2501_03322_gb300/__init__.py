@@ -1,0 +1,224 @@
+"""GB300-native finite-source binary-lens magnification by contour integration.
+
+Thin ctypes binding over the C ABI of ``libtwinkle_gb300.so`` (declared in
+``include/twinkle.h``).  Every step of the computation runs in the library's
+CUDA kernels; this module only marshals arguments.  Arrays may be NumPy arrays
+(host memory: the call is synchronous) or CUDA ``torch`` tensors (device
+memory: the call is asynchronous on the given or current torch stream).
+
+Functions mirror the C entry points:
+
+* ``mag(s, q, rho, y1, y2, rel_tol, ...)``            -- ``tw_mag_ex``
+* ``lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol, ...)`` -- ``tw_lightcurve_ex``
+* ``lightcurve_batch(params, offsets, times, rel_tol, ...)``         -- ``tw_lightcurve_batch``
+
+If the shared library is missing it is built from ``csrc/`` with nvcc; if that
+is impossible the import of the library fails loudly.  There is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+TW_OK, TW_EINVAL, TW_ECUDA, TW_ENOMEM, TW_ETIMEOUT, TW_WCAP = 0, -1, -2, -3, -4, 1
+POS_CAP, POS_IMAGECOUNT, POS_NONFINITE, POS_SOLVER = 1, 2, 4, 8
+PREC_FP64, PREC_MIXED = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (code %d)" % (msg, code))
+        self.code = code
+
+
+class TwOpts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("samples_per_iter", ctypes.c_int),
+        ("max_samples", ctypes.c_int),
+        ("autotune", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("err_out", ctypes.c_void_p),
+        ("nsamp_out", ctypes.c_void_p),
+        ("pos_status", ctypes.c_void_p),
+    ]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded shared library (built on first use if absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                path = _build.build()
+            L = ctypes.CDLL(path)
+            d, i64, P, I = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+            L.tw_opts_default.argtypes = [P]
+            L.tw_opts_default.restype = None
+            L.tw_mag.argtypes = [d, d, d, P, P, i64, d, P]
+            L.tw_mag.restype = I
+            L.tw_mag_ex.argtypes = [d, d, d, P, P, i64, d, P, P]
+            L.tw_mag_ex.restype = I
+            L.tw_lightcurve.argtypes = [d, d, d, d, d, d, d, P, i64, d, P]
+            L.tw_lightcurve.restype = I
+            L.tw_lightcurve_ex.argtypes = [d, d, d, d, d, d, d, P, i64, d, P, P]
+            L.tw_lightcurve_ex.restype = I
+            L.tw_lightcurve_batch.argtypes = [P, P, P, i64, d, P, P]
+            L.tw_lightcurve_batch.restype = I
+            L.tw_status_str.argtypes = [I]
+            L.tw_status_str.restype = ctypes.c_char_p
+            L.tw_version.argtypes = []
+            L.tw_version.restype = I
+            L.tw_last_launch_work.argtypes = [P]
+            L.tw_last_launch_work.restype = I
+            _lib = L
+    return _lib
+
+
+def status_str(code: int) -> str:
+    return lib().tw_status_str(code).decode()
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch_cuda(a):
+        return ctypes.c_void_p(a.data_ptr())
+    if hasattr(a, "data_ptr"):  # CPU torch tensor
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int):
+    if rc < 0:
+        raise TwError(rc, status_str(rc))
+    return rc
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _alloc_like(ref, n, dtype_np, dtype_torch_name):
+    if _is_torch_cuda(ref):
+        import torch
+
+        return torch.empty(n, dtype=getattr(torch, dtype_torch_name), device=ref.device)
+    return np.empty(n, dtype=dtype_np)
+
+
+def make_opts(precision=PREC_FP64, samples_per_iter=64, max_samples=4096, stream=None, err=None, nsamp=None,
+              status=None) -> TwOpts:
+    o = TwOpts()
+    lib().tw_opts_default(ctypes.byref(o))
+    o.precision = int(precision)
+    o.samples_per_iter = int(samples_per_iter)
+    o.max_samples = int(max_samples)
+    o.stream = stream
+    o.err_out = _ptr(err).value if err is not None else None
+    o.nsamp_out = _ptr(nsamp).value if nsamp is not None else None
+    o.pos_status = _ptr(status).value if status is not None else None
+    return o
+
+
+def _stream_of(ref, stream):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    if _is_torch_cuda(ref):
+        import torch
+
+        return torch.cuda.current_stream(ref.device).cuda_stream
+    return None
+
+
+def _prep(arr):
+    if _is_torch_cuda(arr):
+        return arr.contiguous()
+    return _host(arr, np.float64)
+
+
+def last_launch_work() -> dict:
+    """Samples, FP64/FP32 Aberth sweeps and edge evaluations of the last launch."""
+    a = np.zeros(4, np.int64)
+    _check(lib().tw_last_launch_work(a.ctypes.data_as(ctypes.c_void_p)))
+    return dict(samples=int(a[0]), sweeps64=int(a[1]), sweeps32=int(a[2]), edges=int(a[3]))
+
+
+def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64, max_samples=4096,
+        out=None, details=False, stream=None):
+    """Finite-source magnification of positions (y1[i], y2[i]) (tw_mag_ex).
+
+    Returns ``out`` or, with details=True, (out, err, nsamp, status)."""
+    y1, y2 = _prep(y1), _prep(y2)
+    n = int(y1.shape[0])
+    if out is None:
+        out = _alloc_like(y1, n, np.float64, "float64")
+    err = nsamp = status = None
+    if details:
+        err = _alloc_like(y1, n, np.float64, "float64")
+        nsamp = _alloc_like(y1, n, np.int32, "int32")
+        status = _alloc_like(y1, n, np.int8, "int8")
+    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(y1, stream), err, nsamp, status)
+    _check(lib().tw_mag_ex(s, q, rho, _ptr(y1), _ptr(y2), n, rel_tol, _ptr(out), ctypes.byref(o)))
+    return (out, err, nsamp, status) if details else out
+
+
+def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,
+               max_samples=4096, out=None, details=False, stream=None):
+    """Magnification along a straight-line trajectory (tw_lightcurve_ex)."""
+    times = _prep(times)
+    n = int(times.shape[0])
+    if out is None:
+        out = _alloc_like(times, n, np.float64, "float64")
+    err = nsamp = status = None
+    if details:
+        err = _alloc_like(times, n, np.float64, "float64")
+        nsamp = _alloc_like(times, n, np.int32, "int32")
+        status = _alloc_like(times, n, np.int8, "int8")
+    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status)
+    _check(lib().tw_lightcurve_ex(s, q, rho, u0, alpha, t0, tE, _ptr(times), n, rel_tol, _ptr(out), ctypes.byref(o)))
+    return (out, err, nsamp, status) if details else out
+
+
+def lightcurve_batch(params, offsets, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,
+                     max_samples=4096, out=None, details=False, stream=None):
+    """Many light curves in one launch (tw_lightcurve_batch).
+
+    params: [ncurve, 7] (s, q, rho, u0, alpha, t0, tE); offsets: [ncurve + 1] int64."""
+    if _is_torch_cuda(params):
+        params, offsets, times = params.contiguous(), offsets.contiguous(), times.contiguous()
+        total = int(offsets[-1].item())
+    else:
+        params = _host(params, np.float64)
+        offsets = _host(offsets, np.int64)
+        times = _host(times, np.float64)
+        total = int(offsets[-1]) if offsets.size else 0
+    ncurve = int(params.shape[0])
+    if out is None:
+        out = _alloc_like(times, total, np.float64, "float64")
+    err = nsamp = status = None
+    if details:
+        err = _alloc_like(times, total, np.float64, "float64")
+        nsamp = _alloc_like(times, total, np.int32, "int32")
+        status = _alloc_like(times, total, np.int8, "int8")
+    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status)
+    _check(lib().tw_lightcurve_batch(_ptr(params), _ptr(offsets), _ptr(times), ncurve, rel_tol, _ptr(out),
+                                     ctypes.byref(o)))
+    return (out, err, nsamp, status) if details else out

@@ -1,0 +1,447 @@
+// contour.cuh -- contour integration of one source position by one warp.
+//
+// The limb is sampled at angles theta (Sec. 2.3: counter-clockwise from +x,
+// the sort key of the samples).  Each sample holds its five roots, which of
+// them are real images and with which parity, and dz/dtheta and z' ^ z'' of
+// each (lens.cuh).  Each edge between consecutive samples contributes
+//   - for every pair of same-parity images linked across it (Sec. 2.3: same
+//     parity, minimum total distance), p * [trapezium (Eq. 9) + parabolic
+//     correction (Eq. 10, mean of the two forms)], and the error terms
+//     E1..E4 of Eq. 17;
+//   - where the image count changes (a caustic crossing, Sec. 2.3), the extra
+//     positive/negative pair of the five-image sample is joined to itself by
+//     the cross-caustic correction of Eq. 11 with the errors of Eq. 18.
+// The area is the sum over edges (Eq. 8); sampling stops once the summed
+// error is at most rel_tol * area (Sec. 2.5, Sec. 3).  Otherwise new angles
+// are drawn by inverse-transform sampling of the cumulative per-edge error,
+// with each edge's share of the tolerance subtracted first, at
+// (j + 1/2)/n_new quantiles (Sec. 2.5), merged into the sorted order, and only
+// the edges touching new samples are recomputed (Sec. 3).
+//
+// Lane layout: a warp owns one position; the initial 32*SPL uniform samples
+// and every batch of 32*SPL new samples are spread SPL per lane; sums and the
+// cumulative error use warp shuffles.  Per-sample records live in the warp's
+// slot of a global arena (structure of arrays, L2-resident in practice);
+// only the current batch of new angles is staged in shared memory.
+#pragma once
+#include <stdint.h>
+
+#include "lens.cuh"
+
+namespace tw {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Position status bits (mirrors TW_POS_* of twinkle.h).
+enum : int { PS_CAP = 1, PS_IMAGECOUNT = 2, PS_NONFINITE = 4, PS_SOLVER = 8 };
+
+// One warp slot of the sample arena.  Records are indexed by sample slot (the
+// order in which samples were created); ordA/ordB hold slot numbers in theta
+// order; eA/eE the edge from a slot to its successor in theta order.
+struct Arena {
+    double *theta;
+    cxd *roots;  // [slot*5 + i]
+    cxd *zp;     // [slot*5 + i]
+    double *w;   // [slot*5 + i]
+    uint32_t *meta;
+    double *eA;
+    double *eE;
+    uint16_t *ordA;
+    uint16_t *ordB;
+    double *cum;
+};
+
+__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bytes of one warp slot for a sample cap `cap`.
+__host__ __device__ inline size_t arena_slot_bytes(int cap) {
+    size_t c = (size_t)cap;
+    return align256(c * 8) + align256(c * 5 * 16) * 2 + align256(c * 5 * 8) + align256(c * 4) +
+           align256(c * 8) * 2 + align256(c * 2) * 2 + align256(c * 8);
+}
+
+__device__ inline Arena arena_at(char *base, size_t slot_bytes, int cap, int slot) {
+    char *p = base + slot_bytes * (size_t)slot;
+    const size_t c = (size_t)cap;
+    Arena a;
+    a.theta = (double *)p; p += align256(c * 8);
+    a.roots = (cxd *)p; p += align256(c * 5 * 16);
+    a.zp = (cxd *)p; p += align256(c * 5 * 16);
+    a.w = (double *)p; p += align256(c * 5 * 8);
+    a.meta = (uint32_t *)p; p += align256(c * 4);
+    a.eA = (double *)p; p += align256(c * 8);
+    a.eE = (double *)p; p += align256(c * 8);
+    a.ordA = (uint16_t *)p; p += align256(c * 2);
+    a.ordB = (uint16_t *)p; p += align256(c * 2);
+    a.cum = (double *)p;
+    return a;
+}
+
+struct Img {
+    cxd z, zp;
+    double w;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Normal link of image a (angle theta) to image b (theta + dth) of parity sgn:
+// trapezium (Eq. 9) plus the mean of the two parabolic corrections (Eq. 10),
+// and the error terms E1..E4 of Eq. 17.
+__device__ __forceinline__ void link_contrib(const Img &a, const Img &b, double sgn, double dth, double &dA,
+                                             double &dE) {
+    const double d2 = dth * dth, d3 = d2 * dth;
+    const double At = 0.5 * wedge(a.z, b.z);
+    const double p1 = (a.w + b.w) * d3 * (1.0 / 24.0);
+    const cxd dz = b.z - a.z, dzp = b.zp - a.zp;
+    const double p2 = wedge(dz, dzp) * dth * (1.0 / 12.0);
+    const double Ap = 0.5 * (p1 + p2);
+    dA += sgn * (At + Ap);
+    const double e1 = fabs(a.w - b.w) * d3 * (1.0 / 48.0);
+    const double dt = fabs(dot(a.zp, b.zp));
+    const double e2 = 1.5 * fabs(Ap * (norm2(dz) * rcp(fmax(d2 * dt, 1e-300)) - 1.0));
+    const double e3 = 0.1 * fabs(Ap) * d2;
+    const double e4 = fabs(p1 - p2);
+    dE += e1 + e2 + e3 + e4;
+}
+
+// Extra positive (P) / negative (M) pair of a five-image sample next to a
+// caustic crossing, joined to itself: chord from the incoming to the outgoing
+// track (M -> P when the pair is created towards +theta, P -> M when it is
+// destroyed) plus the cross-caustic correction of Eq. 11 and its errors
+// (Eq. 18; the sign inside E2 is - for a creation).  dth is the edge's step.
+__device__ __forceinline__ void pair_contrib(const Img &P, const Img &M, bool creation, double dth, double &dA,
+                                             double &dE) {
+    const cxd dz = P.z - M.z;
+    const double adz = sqrt(norm2(dz));
+    const double dt = fabs(dot(P.zp, M.zp));
+    double tt = (dt > 0.0) ? adz * rsqrt(dt) : 4.0 * dth;  // Eq. 11: |z+ - z-| / sqrt|z'+ . z'-|
+    tt = fmin(tt, 4.0 * dth);
+    const double t3 = tt * tt * tt;
+    const double Ap = (P.w - M.w) * t3 * (1.0 / 24.0);
+    const double At = creation ? 0.5 * wedge(M.z, P.z) : 0.5 * wedge(P.z, M.z);
+    dA += At + Ap;
+    const double e1 = fabs(P.w + M.w) * t3 * (1.0 / 48.0);
+    const cxd dzp = P.zp - M.zp;
+    const double proj = dot(dz, dzp);
+    const double sq = 2.0 * adz * sqrt(dt);
+    const double e2 = 1.5 * fabs(creation ? proj - sq : proj + sq) * tt;
+    const double e3 = 0.1 * fabs(Ap) * dth * dth;
+    dE += e1 + e2 + e3;
+}
+
+// i-th entry of the p-th permutation of N <= 3 elements.
+template <int N>
+__device__ __forceinline__ constexpr int perm_at(int p, int i) {
+    return N == 1 ? 0
+         : N == 2 ? (p == 0 ? i : 1 - i)
+         : (p == 0 ? (i == 0 ? 0 : i == 1 ? 1 : 2)
+          : p == 1 ? (i == 0 ? 0 : i == 1 ? 2 : 1)
+          : p == 2 ? (i == 0 ? 1 : i == 1 ? 0 : 2)
+          : p == 3 ? (i == 0 ? 1 : i == 1 ? 2 : 0)
+          : p == 4 ? (i == 0 ? 2 : i == 1 ? 0 : 1)
+          :          (i == 0 ? 2 : i == 1 ? 1 : 0));
+}
+
+// Link the NX images X of one parity class at the edge's start to the NY
+// images Y of the same class at its end (|NX - NY| <= 1) so that the total
+// distance is minimal (Sec. 2.3; ties go to the lowest permutation).  The one
+// image left over when NX != NY is returned in `left`.
+template <int NX, int NY>
+__device__ __forceinline__ void link_class(const Img *X, const Img *Y, double sgn, double dth, double &dA, double &dE,
+                                           Img &left) {
+    constexpr int N = NX > NY ? NX : NY;
+    constexpr int M = NX > NY ? NY : NX;
+    constexpr int NP = N == 1 ? 1 : (N == 2 ? 2 : 6);
+    float best_cost = 3.0e38f;
+    int best = 0;
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        float cost = 0.f;
+#pragma unroll
+        for (int i = 0; i < M; i++) {
+            const int j = perm_at<N>(p, i);
+            const cxd d = (NX <= NY) ? (Y[j].z - X[i].z) : (Y[i].z - X[j].z);
+            cost += sqrtf((float)norm2(d));
+        }
+        if (cost < best_cost) { best_cost = cost; best = p; }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        if (p == best) {
+#pragma unroll
+            for (int i = 0; i < M; i++) {
+                const int j = perm_at<N>(p, i);
+                if (NX <= NY) link_contrib(X[i], Y[j], sgn, dth, dA, dE);
+                else link_contrib(X[j], Y[i], sgn, dth, dA, dE);
+            }
+            if (NX < NY) left = Y[perm_at<N>(p, N - 1)];
+            if (NX > NY) left = X[perm_at<N>(p, N - 1)];
+        }
+    }
+}
+
+template <int NA, int NB>
+__device__ __forceinline__ void edge_case(const Img *IA, const Img *IB, double dth, double &dA, double &dE) {
+    constexpr int PA = (NA - 1) / 2, PB = (NB - 1) / 2;
+    Img lp, ln;
+    link_class<PA, PB>(IA, IB, 1.0, dth, dA, dE, lp);
+    link_class<NA - PA, NB - PB>(IA + PA, IB + PB, -1.0, dth, dA, dE, ln);
+    if (NA < NB) pair_contrib(lp, ln, true, dth, dA, dE);
+    if (NA > NB) pair_contrib(lp, ln, false, dth, dA, dE);
+}
+
+// Area and error of the edge from sample slot sa to slot sb (angle step dth).
+static __device__ __noinline__ void compute_edge(const Arena &ar, int sa, int sb, double dth, double *outA, double *outE) {
+    const uint32_t ma = ar.meta[sa], mb = ar.meta[sb];
+    const int na = meta_count(ma), nb = meta_count(mb);
+    Img IA[5], IB[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        if (k < na) {
+            const int i = sa * 5 + meta_index(ma, k);
+            IA[k].z = ar.roots[i]; IA[k].zp = ar.zp[i]; IA[k].w = ar.w[i];
+        }
+        if (k < nb) {
+            const int i = sb * 5 + meta_index(mb, k);
+            IB[k].z = ar.roots[i]; IB[k].zp = ar.zp[i]; IB[k].w = ar.w[i];
+        }
+    }
+    double dA = 0.0, dE = 0.0;
+    if (na == 3 && nb == 3) edge_case<3, 3>(IA, IB, dth, dA, dE);
+    else if (na == 5 && nb == 5) edge_case<5, 5>(IA, IB, dth, dA, dE);
+    else if (na == 3) edge_case<3, 5>(IA, IB, dth, dA, dE);
+    else edge_case<5, 3>(IA, IB, dth, dA, dE);
+    // a sample that failed the image-count check: keep refining around it
+    if ((ma | mb) >> 31) dE += fabs(dA);
+    *outA = dA;
+    *outE = dE;
+}
+
+// One limb sample: coefficients, roots (warm-started from z), classification,
+// derivatives, stored in slot `slot`.  Returns the sample's status bits.
+// Work done by one warp on one position (for FLOP accounting).
+struct WorkCount {
+    int sw64 = 0, sw32 = 0, edges = 0;
+};
+
+template <int PREC>
+__device__ __forceinline__ int limb_sample(const LensK &L, double th, cxd z[5], const Arena &ar, int slot,
+                                           WorkCount &wc) {
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    const cxd y = {L.y0.x + L.rho * cs, L.y0.y + L.rho * sn};
+    const cxd dzeta = {-L.rho * sn, L.rho * cs}; // zeta' = i rho e^{i theta}
+    cxd c[6];
+    eq6_coeffs(L.s, L.m2, y, c);
+    float dpa[5];
+    int f = solve_quintic<PREC>(c, z, dpa, 60, wc.sw64, wc.sw32);
+    SampleRefs o = {&ar.theta[slot], &ar.roots[slot * 5], &ar.zp[slot * 5], &ar.w[slot * 5], &ar.meta[slot]};
+    f |= classify_store(L, y, dzeta, c, z, dpa, th, o);
+    return f;
+}
+
+struct WarpStage {
+    double theta_new[256];
+    uint16_t pos_new[256];
+};
+
+struct PosResult {
+    double area, err;
+    int nsamp, status;
+    WorkCount work;  // summed over the warp
+};
+
+template <int PREC, int SPL>
+__device__ PosResult integrate_position(const LensK &L, double tol, int cap, const Arena &ar, WarpStage &ws) {
+    constexpr int SPI = 32 * SPL;
+    const int lane = threadIdx.x & 31;
+    const double twopi = 6.283185307179586476925287;
+    const double minsep = 1e-15 / L.rho + 1e-14;
+    int flags = 0;
+    WorkCount wc;
+
+    // images of the source centre: the warm start of the first samples
+    cxd cc[6], zc[5];
+    eq6_coeffs(L.s, L.m2, L.y0, cc);
+    initial_roots(L.s, L.y0, zc);
+    {
+        float dpa[5];
+        int c64 = 0, c32 = 0;
+        flags |= solve_quintic<0>(cc, zc, dpa, 200, c64, c32);
+        if (lane == 0) wc.sw64 += c64;
+    }
+#pragma unroll
+    for (int t = 0; t < SPL; t++) {
+        const int k = lane * SPL + t;
+        cxd z[5] = {zc[0], zc[1], zc[2], zc[3], zc[4]};
+        flags |= limb_sample<PREC>(L, twopi * k / SPI, z, ar, k, wc);
+        ar.ordA[k] = (uint16_t)k;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < SPL; t++) {
+        const int k = lane * SPL + t;
+        compute_edge(ar, k, (k + 1 == SPI) ? 0 : k + 1, twopi / SPI, &ar.eA[k], &ar.eE[k]);
+        wc.edges++;
+    }
+    __syncwarp();
+
+    int N = SPI, nslot = SPI;
+    uint16_t *ordA = ar.ordA, *ordB = ar.ordB;
+    double A = 0.0, E = 0.0;
+    for (;;) {
+        double a = 0.0, e = 0.0;
+        for (int p = lane; p < N; p += 32) {
+            const int sl = ordA[p];
+            a += ar.eA[sl];
+            e += ar.eE[sl];
+        }
+        A = warp_sum(a);
+        E = warp_sum(e);
+        if (!(E > tol * fabs(A))) break;          // converged (or non-finite)
+        if (nslot + SPI > cap) { flags |= PS_CAP; break; }
+
+        // cumulative error in theta order, each edge less its share of the tolerance
+        const double thr = tol * fabs(A) / N;
+        const int chunk = (N + 31) >> 5;
+        const int p0 = min(lane * chunk, N), p1 = min(p0 + chunk, N);
+        double run = 0.0;
+        for (int p = p0; p < p1; p++) {
+            run += fmax(ar.eE[ordA[p]] - thr, 0.0);
+            ar.cum[p] = run;
+        }
+        double incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const double W = __shfl_sync(FULL, incl, 31);
+        const double excl = incl - run;
+        for (int p = p0; p < p1; p++) ar.cum[p] += excl;
+        __syncwarp();
+
+        // inverse transform at quantiles (j + 1/2)/SPI with linear interpolation
+        double tn[SPL];
+        int tp[SPL];
+        bool tk[SPL];
+#pragma unroll
+        for (int t = 0; t < SPL; t++) {
+            const int j = lane * SPL + t;
+            const double target = (j + 0.5) * (W / SPI);
+            int lo = 0, hi = N - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ar.cum[mid] > target) hi = mid; else lo = mid + 1;
+            }
+            const int sa = ordA[lo];
+            const double wp = fmax(ar.eE[sa] - thr, 0.0);
+            double frac = (wp > 0.0) ? (target - (ar.cum[lo] - wp)) / wp : 0.5;
+            frac = fmin(fmax(frac, 0.0), 1.0);
+            const double ta = ar.theta[sa];
+            const double tb = (lo + 1 < N) ? ar.theta[ordA[lo + 1]] : twopi;
+            tn[t] = ta + frac * (tb - ta);
+            tp[t] = lo;
+            tk[t] = (tn[t] - ta > minsep) && (tb - tn[t] > minsep);
+        }
+        // drop a quantile that coincides with the previous one
+#pragma unroll
+        for (int t = 0; t < SPL; t++) {
+            double pth = __shfl_up_sync(FULL, tn[SPL - 1], 1);
+            int ppos = __shfl_up_sync(FULL, tp[SPL - 1], 1);
+            if (t > 0) { pth = tn[t - 1]; ppos = tp[t - 1]; }
+            const bool has_prev = (t > 0) || (lane > 0);
+            if (has_prev && ppos == tp[t] && fabs(tn[t] - pth) <= minsep) tk[t] = false;
+        }
+        // compaction of the kept angles, in quantile order
+        const unsigned lt = (1u << lane) - 1u;
+        int before = 0, m = 0;
+#pragma unroll
+        for (int t = 0; t < SPL; t++) {
+            const unsigned b = __ballot_sync(FULL, tk[t]);
+            before += __popc(b & lt);
+            m += __popc(b);
+        }
+        int rk[SPL];
+        {
+            int own = 0;
+#pragma unroll
+            for (int t = 0; t < SPL; t++) {
+                rk[t] = before + own;
+                own += tk[t] ? 1 : 0;
+            }
+        }
+        if (m == 0) { flags |= PS_CAP; break; } // no room left between samples
+#pragma unroll
+        for (int t = 0; t < SPL; t++)
+            if (tk[t]) {
+                ws.theta_new[rk[t]] = tn[t];
+                ws.pos_new[rk[t]] = (uint16_t)tp[t];
+            }
+        __syncwarp();
+
+        // new samples, warm-started from the sample at the start of their interval
+#pragma unroll
+        for (int t = 0; t < SPL; t++)
+            if (tk[t]) {
+                const int sa = ordA[tp[t]];
+                cxd z[5];
+#pragma unroll
+                for (int i = 0; i < 5; i++) z[i] = ar.roots[sa * 5 + i];
+                flags |= limb_sample<PREC>(L, tn[t], z, ar, nslot + rk[t], wc);
+            }
+        // merge into theta order
+        for (int p = p0; p < p1; p++) {
+            int lo = 0, hi = m;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ws.pos_new[mid] < p) lo = mid + 1; else hi = mid;
+            }
+            ordB[p + lo] = ordA[p];
+        }
+#pragma unroll
+        for (int t = 0; t < SPL; t++)
+            if (tk[t]) ordB[tp[t] + 1 + rk[t]] = (uint16_t)(nslot + rk[t]);
+        __syncwarp();
+        uint16_t *tmp = ordA; ordA = ordB; ordB = tmp;
+        const int nslot_old = nslot;
+        N += m;
+        nslot += m;
+
+        // edges touching the new samples
+#pragma unroll
+        for (int t = 0; t < SPL; t++)
+            if (tk[t]) {
+                const int P = tp[t] + 1 + rk[t];
+                const int sl = nslot_old + rk[t];
+                const int nx = (P + 1 < N) ? P + 1 : 0;
+                const int sb = ordA[nx];
+                const double tb = (P + 1 < N) ? ar.theta[sb] : twopi;
+                compute_edge(ar, sl, sb, tb - tn[t], &ar.eA[sl], &ar.eE[sl]);
+                wc.edges++;
+                const bool first = (rk[t] == 0) || (ws.pos_new[rk[t] - 1] != tp[t]);
+                if (first) {
+                    const int so = ordA[P - 1];
+                    compute_edge(ar, so, sl, tn[t] - ar.theta[so], &ar.eA[so], &ar.eE[so]);
+                    wc.edges++;
+                }
+            }
+        __syncwarp();
+    }
+    flags = __reduce_or_sync(FULL, flags);
+    PosResult r;
+    r.work.sw64 = __reduce_add_sync(FULL, wc.sw64);
+    r.work.sw32 = __reduce_add_sync(FULL, wc.sw32);
+    r.work.edges = __reduce_add_sync(FULL, wc.edges);
+    r.area = A;
+    r.err = E;
+    r.nsamp = N;
+    r.status = flags;
+    return r;
+}
+
+}  // namespace tw

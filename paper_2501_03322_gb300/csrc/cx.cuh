@@ -1,0 +1,72 @@
+// cx.cuh -- minimal complex arithmetic for the device code (FP64 and FP32).
+//
+// Plain structs so that everything stays in registers; reciprocals use the
+// correctly rounded CUDA intrinsics.  The FP32 division rescales its divisor
+// first because polynomial values near a root of a low-mass-ratio lens can be
+// small enough for |b|^2 to underflow in single precision.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace tw {
+
+template <typename T>
+struct cx {
+    T x, y;
+};
+using cxd = cx<double>;
+using cxf = cx<float>;
+
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T a, T b) { return cx<T>{a, b}; }
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.x, s * a.y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.x, -a.y}; }
+template <typename T>
+__device__ __forceinline__ T norm2(cx<T> a) { return a.x * a.x + a.y * a.y; }
+// a ^ b = Re(a) Im(b) - Im(a) Re(b)  (the wedge product of Eq. 8)
+template <typename T>
+__device__ __forceinline__ T wedge(cx<T> a, cx<T> b) { return a.x * b.y - a.y * b.x; }
+// real dot product Re(conj(a) b)
+template <typename T>
+__device__ __forceinline__ T dot(cx<T> a, cx<T> b) { return a.x * b.x + a.y * b.y; }
+
+__device__ __forceinline__ double rcp(double v) { return __drcp_rn(v); }
+__device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+
+__device__ __forceinline__ cxd inv(cxd a) {
+    double r = rcp(fmax(norm2(a), 1e-300));
+    return {a.x * r, -a.y * r};
+}
+__device__ __forceinline__ cxd cdiv(cxd a, cxd b) {
+    double r = rcp(fmax(norm2(b), 1e-300));
+    return {(a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r};
+}
+__device__ __forceinline__ cxf inv(cxf a) {
+    float sc = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), 1e-30f);
+    float k = rcp(sc);
+    cxf b = {a.x * k, a.y * k};
+    float r = rcp(norm2(b)) * k;
+    return {b.x * r, -b.y * r};
+}
+__device__ __forceinline__ cxf cdiv(cxf a, cxf b) {
+    float sc = fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), 1e-30f);
+    float k = rcp(sc);
+    cxf bb = {b.x * k, b.y * k};
+    cxf aa = {a.x * k, a.y * k};
+    float r = rcp(norm2(bb));
+    return {(aa.x * bb.x + aa.y * bb.y) * r, (aa.y * bb.x - aa.x * bb.y) * r};
+}
+
+__device__ __forceinline__ cxf to_f(cxd a) { return {(float)a.x, (float)a.y}; }
+__device__ __forceinline__ cxd to_d(cxf a) { return {(double)a.x, (double)a.y}; }
+
+}  // namespace tw

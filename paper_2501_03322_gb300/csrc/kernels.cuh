@@ -1,0 +1,160 @@
+// kernels.cuh -- the contour-integration kernel and its work sources.
+//
+// Work distribution: a persistent grid (a whole number of CTAs per SM, 4
+// warps each) whose warps take source positions one at a time from a global
+// atomic counter (work stealing).  This replaces the paper's multi-stream
+// dispatch and its re-dispatched list of unfinished sources (Sec. 3, Sec. 4.1):
+// a warp that finishes a cheap position immediately takes the next one, so
+// expensive caustic-crossing positions do not stall an SM.  Light curves are
+// flattened into (curve, time) work items whose trajectory point is computed
+// when the item is taken.
+//
+// Each (precision, samples-per-lane) instance is compiled in its own
+// translation unit (k_*.cu) and exposed through a plain host launcher, so the
+// instances build in parallel.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "contour.cuh"
+
+namespace tw {
+
+constexpr int TPB = 128;  // 4 warps per CTA
+constexpr int WPB = TPB / 32;
+
+// Where the positions of a launch come from.
+struct WorkSrc {
+    int kind;  // 0: one lens, arrays of positions; 1: one light curve; 2: batch of light curves
+    int64_t n;
+    double s, q, rho;                      // kinds 0 and 1
+    const double *y1, *y2;                 // kind 0
+    double u0, alpha, t0, tE;              // kind 1
+    const double *times;                   // kinds 1 and 2
+    const double *params;                  // kind 2: [ncurve][7]
+    const int64_t *offsets;                // kind 2: [ncurve + 1]
+    int64_t ncurve;
+};
+
+struct KParams {
+    WorkSrc src;
+    double *out, *err;
+    int32_t *nsamp;
+    int8_t *pstat;
+    char *arena;
+    size_t slot_bytes;
+    int cap;
+    double tol;
+    unsigned long long *counter;  // [0]: next work item; [1..4]: samples, FP64 sweeps, FP32 sweeps, edges
+};
+
+struct PosIn {
+    double s, q, rho, y1, y2;
+};
+
+__device__ __forceinline__ bool pos_ok(double v) { return isfinite(v); }
+
+// Straight-line trajectory (convention of twinkle.h).
+__device__ __forceinline__ void trajectory(double u0, double alpha, double t0, double tE, double t, double &y1,
+                                           double &y2) {
+    const double tau = (t - t0) / tE;
+    double sa, ca;
+    sincos(alpha, &sa, &ca);
+    y1 = tau * ca - u0 * sa;
+    y2 = tau * sa + u0 * ca;
+}
+
+__device__ __forceinline__ bool fetch_position(const WorkSrc &w, int64_t idx, PosIn &P) {
+    if (w.kind == 0) {
+        P.s = w.s; P.q = w.q; P.rho = w.rho;
+        P.y1 = w.y1[idx];
+        P.y2 = w.y2[idx];
+    } else if (w.kind == 1) {
+        P.s = w.s; P.q = w.q; P.rho = w.rho;
+        trajectory(w.u0, w.alpha, w.t0, w.tE, w.times[idx], P.y1, P.y2);
+    } else {
+        // curve k with offsets[k] <= idx < offsets[k+1]
+        int64_t lo = 0, hi = w.ncurve - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (w.offsets[mid] <= idx) lo = mid; else hi = mid - 1;
+        }
+        const double *pr = w.params + 7 * lo;
+        P.s = pr[0]; P.q = pr[1]; P.rho = pr[2];
+        const double tE = pr[6];
+        if (!(tE > 0.0) || !isfinite(tE)) return false;
+        trajectory(pr[3], pr[4], pr[5], tE, w.times[idx], P.y1, P.y2);
+    }
+    return P.s > 0.0 && P.q > 0.0 && P.rho > 0.0 && isfinite(P.s) && isfinite(P.q) && isfinite(P.rho) &&
+           pos_ok(P.y1) && pos_ok(P.y2);
+}
+
+template <int PREC, int SPL>
+__global__ void __launch_bounds__(TPB) contour_kernel(KParams kp) {
+    __shared__ WarpStage stage[WPB];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * WPB + wib;
+    const Arena ar = arena_at(kp.arena, kp.slot_bytes, kp.cap, gw);
+    for (;;) {
+        unsigned long long idx = 0;
+        if (lane == 0) idx = atomicAdd(kp.counter, 1ull);
+        idx = __shfl_sync(FULL, idx, 0);
+        if (idx >= (unsigned long long)kp.src.n) break;
+        PosIn P;
+        const bool valid = fetch_position(kp.src, (int64_t)idx, P);
+        double mu = __longlong_as_double(0x7ff8000000000000ll), err = mu;
+        int nsamp = 0, status = PS_NONFINITE;
+        if (valid) {
+            LensK L;
+            L.s = P.s;
+            L.m1 = 1.0 / (1.0 + P.q);
+            L.m2 = P.q / (1.0 + P.q);
+            L.rho = P.rho;
+            L.y0 = {P.y1 - P.s / (1.0 + P.q), P.y2};  // centre-of-mass -> secondary frame
+            const PosResult r = integrate_position<PREC, SPL>(L, kp.tol, kp.cap, ar, stage[wib]);
+            const double area_src = 3.141592653589793238 * P.rho * P.rho;
+            mu = r.area / area_src;
+            err = r.err / area_src;
+            nsamp = r.nsamp;
+            status = r.status;
+            if (lane == 0) {
+                atomicAdd(kp.counter + 1, (unsigned long long)r.nsamp);
+                atomicAdd(kp.counter + 2, (unsigned long long)r.work.sw64);
+                atomicAdd(kp.counter + 3, (unsigned long long)r.work.sw32);
+                atomicAdd(kp.counter + 4, (unsigned long long)r.work.edges);
+            }
+            if (!isfinite(mu)) { status |= PS_NONFINITE; mu = __longlong_as_double(0x7ff8000000000000ll); }
+        }
+        if (lane == 0) {
+            kp.out[idx] = mu;
+            if (kp.err) kp.err[idx] = err;
+            if (kp.nsamp) kp.nsamp[idx] = nsamp;
+            if (kp.pstat) kp.pstat[idx] = (int8_t)status;
+        }
+    }
+}
+
+
+// Host launcher and occupancy query of one kernel instance.
+#define TW_DEFINE_LAUNCHER(PREC, SPL)                                                              \
+    cudaError_t launch_contour_##PREC##_##SPL(unsigned blocks, cudaStream_t st, const KParams &kp) { \
+        contour_kernel<PREC, SPL><<<blocks, TPB, 0, st>>>(kp);                                      \
+        return cudaGetLastError();                                                                  \
+    }                                                                                               \
+    cudaError_t occupancy_contour_##PREC##_##SPL(int *occ) {                                        \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, contour_kernel<PREC, SPL>, TPB, 0); \
+    }
+
+#define TW_DECLARE_LAUNCHER(PREC, SPL)                                                           \
+    cudaError_t launch_contour_##PREC##_##SPL(unsigned blocks, cudaStream_t st, const KParams &kp); \
+    cudaError_t occupancy_contour_##PREC##_##SPL(int *occ);
+
+TW_DECLARE_LAUNCHER(0, 1)
+TW_DECLARE_LAUNCHER(0, 2)
+TW_DECLARE_LAUNCHER(0, 4)
+TW_DECLARE_LAUNCHER(1, 1)
+TW_DECLARE_LAUNCHER(1, 2)
+TW_DECLARE_LAUNCHER(1, 4)
+
+}  // namespace tw

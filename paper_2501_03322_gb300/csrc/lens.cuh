@@ -1,0 +1,314 @@
+// lens.cuh -- point-source images of one limb sample, on the device.
+//
+// Frame: origin on the secondary (the frame of Eq. 6): the primary (mass m1)
+// sits at -s, the secondary (mass m2) at 0; y = zeta - z2 and eta = z - z2,
+// z2 = s/(1+q) being the secondary's centre-of-mass coordinate (Eq. 2).
+//
+// Steps, each following the paper:
+//   coefficients   Eq. 6 (cancellation-free form), FP64
+//   roots          Aberth-Ehrlich simultaneous iteration, warm-started from a
+//                  neighbouring sample's roots.  FP64 mode iterates in FP64;
+//                  mixed mode iterates in FP32 and then takes one FP64 Newton
+//                  step per root (falling back to FP64 iteration when the
+//                  quadratic-convergence bound is not met).  The paper uses
+//                  the Skowron-Gould Newton/Laguerre solver (Sec. 2.2); any
+//                  solver returning the five roots computes the same thing.
+//   ghost test     residual R_i of Eq. 12 in FP64; ghosts are the pair whose
+//                  residuals are equal and opposite (Sec. 2.4.1) and well above
+//                  the round-off level of those roots
+//   parity         sign of J (Eq. 7); a sample is accepted when it has 3 or 5
+//                  real images with parity sum -1 (Sec. 2.3)
+//   derivatives    dz/dtheta = (zeta' - conj(f') conj(zeta'))/J and
+//                  z' ^ z'' = (rho^2 + Im(z'^2 zeta' f''))/J  (Eq. 10)
+#pragma once
+#include <stdint.h>
+
+#include "cx.cuh"
+
+namespace tw {
+
+// Per-sample status bits (merged into the per-position status).
+enum : int { SF_IMAGECOUNT = 2, SF_SOLVER = 8 };
+
+struct LensK {
+    double s, m1, m2; // separation and normalised masses (Eq. 2)
+    double rho;       // source radius
+    cxd y0;           // source centre in the secondary's frame
+};
+
+// Eq. 6.  "Im(y) i" is read as i Im(y); m1 = 1 - m2 has been substituted.
+__device__ __forceinline__ void eq6_coeffs(double s, double m2, cxd y, cxd c[6]) {
+    const cxd yb = conj(y);
+    const cxd vc = {yb.x + s, yb.y};              // v_c = conj(y) + s
+    const cxd vp = {1.0 + s * yb.x, s * yb.y};    // v_p = 1 + s conj(y)
+    const double im = y.y;
+    const cxd iim = {0.0, im};                    // i Im(y)
+    const double m2s = m2 * s;
+    c[5] = {-(yb.x * vc.x - yb.y * vc.y), -(yb.x * vc.y + yb.y * vc.x)};
+    // c4 = (conj(y) y - 1 - 2 s conj(y)) v_c + m2 s
+    const cxd t4 = {norm2(y) - 1.0 - 2.0 * s * yb.x, -2.0 * s * yb.y};
+    c[4] = t4 * vc;
+    c[4].x += m2s;
+    // c3 = (2y - s)(v_p v_c + 2 i Im y - m2 s) + 4 (m2 s - y) i Im y
+    const cxd a3 = {2.0 * y.x - s, 2.0 * y.y};
+    cxd b3 = vp * vc;
+    b3.x -= m2s;
+    b3.y += 2.0 * im;
+    const cxd c3b = {m2s - y.x, -y.y};
+    c[3] = a3 * b3 + 4.0 * (c3b * iim);
+    // c2 = Re(v_p)^2 Re(v_c) + i Im(y) Re(v_p) Re(1 - s y) + s Im(y)^2 (2 + s v_c)
+    //      + m2 s [2 conj(y) (y - s) - (1 - s y)]
+    const double rvp = vp.x, rvc = vc.x;
+    cxd c2 = {rvp * rvp * rvc, im * rvp * (1.0 - s * y.x)};
+    const double sim2 = s * im * im;
+    c2.x += sim2 * (2.0 + s * vc.x);
+    c2.y += sim2 * (s * vc.y);
+    const cxd ymS = {y.x - s, y.y};
+    cxd t2 = 2.0 * (yb * ymS);
+    t2.x -= 1.0 - s * y.x;
+    t2.y -= -s * y.y;
+    c[2] = c2 + m2s * t2;
+    // c1 = m2 s [(s + 2y) v_p + s (2 s i Im y - m2)]
+    const cxd s2y = {s + 2.0 * y.x, 2.0 * y.y};
+    cxd t1 = s2y * vp;
+    t1.x += s * (-m2);
+    t1.y += s * (2.0 * s * im);
+    c[1] = m2s * t1;
+    // c0 = s^2 m2^2 y
+    c[0] = (m2s * m2s) * y;
+}
+
+// One Gauss-Seidel sweep of the Aberth-Ehrlich iteration on the quintic c.
+// dpa[i] receives |p'(z_i)|.  Returns true when every correction is below
+// max(rtol |z_i|, 8 eps B_i/|p'(z_i)|), B_i being the Horner round-off bound
+// sum_k |c_k| |z_i|^k (the second term is the attainable accuracy of a
+// near-multiple root).
+template <typename T>
+__device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6], cx<T> z[5], float dpa[5],
+                                             float rtol, float eps) {
+    bool conv = true;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        cx<T> p = c[5], d = {T(0), T(0)};
+        const float az = sqrtf((float)norm2(z[i]));
+        float B = ca[5];
+#pragma unroll
+        for (int k = 4; k >= 0; k--) {
+            d = d * z[i] + p;
+            p = p * z[i] + c[k];
+            B = B * az + ca[k];
+        }
+        const cx<T> ratio = cdiv(p, d);
+        cx<T> S = {T(0), T(0)};
+#pragma unroll
+        for (int j = 0; j < 5; j++)
+            if (j != i) S = S + inv(z[i] - z[j]);
+        const cx<T> rs = ratio * S;
+        const cx<T> w = cdiv(ratio, cx<T>{T(1) - rs.x, -rs.y});
+        z[i] = z[i] - w;
+        const float dabs = sqrtf((float)norm2(d));
+        dpa[i] = dabs;
+        const float wa = sqrtf((float)norm2(w));
+        const float thr = fmaxf(rtol * az, 8.0f * eps * B / fmaxf(dabs, 1e-37f));
+        conv = conv && (wa <= thr);
+    }
+    return conv;
+}
+
+// Aberth starting points on a circle enclosing the roots (used once per
+// position, for the source centre).
+__device__ __forceinline__ void initial_roots(double s, cxd y0, cxd z[5]) {
+    const double r = 1.5 * (1.0 + s + sqrt(norm2(y0)));
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        double sn, cs;
+        sincos(6.283185307179586 * k / 5.0 + 0.4, &sn, &cs);
+        z[k] = {-0.5 * s + r * cs, r * sn};
+    }
+}
+
+__device__ __forceinline__ void abs_coeffs(const cxd c[6], float ca[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) ca[k] = (float)sqrt(norm2(c[k]));
+}
+
+// Roots of the quintic c starting from z.  PREC 0: FP64 iteration; PREC 1:
+// FP32 iteration + FP64 Newton step per root, with FP64 iteration as the
+// fallback.  Returns SF_SOLVER when the iteration limit was reached.
+template <int PREC>
+__device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa[5], int maxit, int &sw64, int &sw32) {
+    float ca[6];
+    abs_coeffs(c, ca);
+    if (PREC == 1) {
+        // scale to unit largest coefficient so FP32 neither under- nor overflows
+        float cm = fmaxf(fmaxf(fmaxf(ca[0], ca[1]), fmaxf(ca[2], ca[3])), fmaxf(ca[4], ca[5]));
+        const double sc = 1.0 / (double)cm;
+        cxf cf[6];
+        float caf[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            cf[k] = to_f(sc * c[k]);
+            caf[k] = (float)(sc * ca[k]);
+        }
+        cxf zf[5];
+#pragma unroll
+        for (int i = 0; i < 5; i++) zf[i] = to_f(z[i]);
+        bool conv = false;
+        for (int it = 0; it < 40 && !conv; it++) {
+            conv = aberth_sweep<float>(cf, caf, zf, dpa, 2e-6f, 6e-8f);
+            sw32++;
+        }
+        // one FP64 Newton step per root; accepted when |step|^2 * sum_j 1/|z_i - z_j|
+        // (the quadratic error bound) is below the FP64 target
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            cxd zi = to_d(zf[i]);
+            cxd p = c[5], d = {0.0, 0.0};
+            const float az = sqrtf(norm2(zf[i]));
+            float B = ca[5];
+#pragma unroll
+            for (int k = 4; k >= 0; k--) {
+                d = d * zi + p;
+                p = p * zi + c[k];
+                B = B * az + ca[k];
+            }
+            const cxd step = cdiv(p, d);
+            z[i] = zi - step;
+            float K = 0.f;
+#pragma unroll
+            for (int j = 0; j < 5; j++)
+                if (j != i) K += rsqrtf(fmaxf(norm2(zf[i] - zf[j]), 1e-37f));
+            const float st2 = (float)norm2(step);
+            const float dabs = sqrtf((float)norm2(d));
+            dpa[i] = dabs;
+            const float tgt = fmaxf(1e-14f * az, 8.0f * 1.1e-16f * B / fmaxf(dabs, 1e-37f));
+            ok = ok && (st2 * K <= tgt) && isfinite(st2);
+        }
+        if (ok) return 0;
+        // fallback: FP64 iteration from the FP32 roots
+#pragma unroll
+        for (int i = 0; i < 5; i++) z[i] = to_d(zf[i]);
+    }
+    for (int it = 0; it < maxit; it++) {
+        sw64++;
+        if (aberth_sweep<double>(c, ca, z, dpa, 1e-14f, 1.1e-16f)) return 0;
+    }
+    return SF_SOLVER;
+}
+
+// Storage of one limb sample in a position's arena (see contour.cuh).
+struct SampleRefs {
+    double *theta;
+    cxd *roots;   // [5] all roots (warm starts for neighbours)
+    cxd *zp;      // [5] dz/dtheta of each root (meaningful for real images)
+    double *w;    // [5] z' ^ z''
+    uint32_t *meta;
+};
+
+// Meta word: bits 0-2 number of real images (3 or 5); bits 3.. the root index
+// (3 bits each) of the real images, positive parity first; bit 31 set when the
+// sample failed the image-count/parity check.
+__device__ __forceinline__ int meta_count(uint32_t m) { return (int)(m & 7u); }
+__device__ __forceinline__ int meta_index(uint32_t m, int k) { return (int)((m >> (3 + 3 * k)) & 7u); }
+
+// Classify the roots z of the sample at limb point y (secondary frame), with
+// limb tangent dzeta = i rho e^{i theta}; compute derivatives; store.
+// Returns the sample's status bits.
+__device__ __forceinline__ int classify_store(const LensK& L, cxd y, cxd dzeta, const cxd c[6], const cxd z[5],
+                                              const float dpa[5], double theta, SampleRefs out) {
+    cxd R[5], f1[5], f2[5];
+    double aR[5], J[5];
+    float noise[5];
+    float ca[6];
+    abs_coeffs(c, ca);
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const cxd d1 = inv(cxd{z[i].x + L.s, z[i].y}); // 1/(eta + s) = -1/(z1 - z)
+        const cxd d2 = inv(z[i]);                      // 1/eta      = -1/(z2 - z)
+        const cxd g = L.m1 * d1 + L.m2 * d2;           // = -f(z)
+        R[i] = y - z[i] + conj(g);                     // Eq. 12
+        aR[i] = norm2(R[i]);
+        const cxd d1s = d1 * d1, d2s = d2 * d2;
+        f1[i] = L.m1 * d1s + L.m2 * d2s;               // f'(z)
+        f2[i] = -2.0 * (L.m1 * (d1s * d1) + L.m2 * (d2s * d2)); // f''(z)
+        J[i] = 1.0 - norm2(f1[i]);                     // Eq. 7
+        const float az = sqrtf((float)norm2(z[i]));
+        float B = ca[5];
+#pragma unroll
+        for (int k = 4; k >= 0; k--) B = B * az + ca[k];
+        noise[i] = 1.1e-16f * B * (1.0f + (float)(fabs(f1[i].x) + fabs(f1[i].y))) / fmaxf(dpa[i], 1e-37f);
+    }
+    int rank[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < 5; j++)
+            if (j != i) r += (aR[j] < aR[i]) || (aR[j] == aR[i] && j < i);
+        rank[i] = r;
+    }
+    cxd R4 = {0, 0}, R5 = {0, 0};
+    double a3 = 0, a4 = 0, a5 = 0;
+    float n45 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        if (rank[i] == 2) a3 = aR[i];
+        if (rank[i] == 3) { R4 = R[i]; a4 = aR[i]; n45 = fmaxf(n45, noise[i]); }
+        if (rank[i] == 4) { R5 = R[i]; a5 = aR[i]; n45 = fmaxf(n45, noise[i]); }
+    }
+    // Sec. 2.4.1: a ghost pair has equal and opposite residuals far above the
+    // round-off level of those roots
+    const bool ghost = (norm2(R4 + R5) < 1e-4 * a5) && (a4 > 1e4 * (double)n45 * (double)n45) && (a4 > 100.0 * a3);
+    int count = ghost ? 3 : 5;
+    int flags = 0;
+    // Sec. 2.3: 3 real images with one positive, or 5 with two positive
+    int npos3 = 0, npos5 = 0;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        npos3 += (rank[i] < 3 && J[i] > 0);
+        npos5 += (J[i] > 0);
+    }
+    const bool ok3 = (npos3 == 1), ok5 = (npos5 == 2);
+    if (count == 3 && !ok3 && ok5) count = 5;
+    else if (count == 5 && !ok5 && ok3) count = 3;
+    else if (!(count == 3 ? ok3 : ok5)) flags |= SF_IMAGECOUNT;
+
+    // derivatives (Eq. 10, with conj(f') in dz/dtheta) and storage
+    const double rho2 = L.rho * L.rho;
+    uint32_t meta = (uint32_t)count;
+    int kp = 0, kn = (count - 1) / 2;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        double Ji = J[i];
+        if (fabs(Ji) < 1e-300) Ji = copysign(1e-300, Ji);
+        const double rJ = rcp(Ji);
+        const cxd num = dzeta - conj(f1[i]) * conj(dzeta);
+        const cxd zp = rJ * num;
+        const cxd t = (zp * zp) * (dzeta * f2[i]);
+        const double wv = (rho2 + t.y) * rJ;
+        out.roots[i] = z[i];
+        out.zp[i] = zp;
+        out.w[i] = wv;
+        if (rank[i] < count) {
+            if (J[i] > 0 && kp < (count - 1) / 2) { meta |= (uint32_t)i << (3 + 3 * kp); kp++; }
+            else if (J[i] <= 0 && kn < count) { meta |= (uint32_t)i << (3 + 3 * kn); kn++; }
+            else flags |= SF_IMAGECOUNT;
+        }
+    }
+    if (flags & SF_IMAGECOUNT) {
+        // fall back to the residual order alone so the sample still has `count` images
+        meta = (uint32_t)count | (1u << 31);
+        int k = 0;
+#pragma unroll
+        for (int r = 0; r < 5; r++)
+#pragma unroll
+            for (int i = 0; i < 5; i++)
+                if (rank[i] == r && r < count) { meta |= (uint32_t)i << (3 + 3 * k); k++; }
+    }
+    *out.meta = meta;
+    *out.theta = theta;
+    return flags;
+}
+
+}  // namespace tw

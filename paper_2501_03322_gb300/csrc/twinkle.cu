@@ -1,0 +1,339 @@
+// twinkle.cu -- launch runtime and C ABI of libtwinkle_gb300.so (host code).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/twinkle.h"
+#include "kernels.cuh"
+
+namespace tw {
+
+// ---------------------------------------------------------------- runtime
+
+typedef cudaError_t (*launch_fn)(unsigned, cudaStream_t, const KParams &);
+typedef cudaError_t (*occ_fn)(int *);
+
+static void pick_kernel(int prec, int spl, launch_fn *lf, occ_fn *of) {
+    if (prec == 0) {
+        if (spl == 1) { *lf = launch_contour_0_1; *of = occupancy_contour_0_1; }
+        else if (spl == 2) { *lf = launch_contour_0_2; *of = occupancy_contour_0_2; }
+        else { *lf = launch_contour_0_4; *of = occupancy_contour_0_4; }
+    } else {
+        if (spl == 1) { *lf = launch_contour_1_1; *of = occupancy_contour_1_1; }
+        else if (spl == 2) { *lf = launch_contour_1_2; *of = occupancy_contour_1_2; }
+        else { *lf = launch_contour_1_4; *of = occupancy_contour_1_4; }
+    }
+}
+
+struct DevState {
+    bool init = false;
+    int nsm = 0;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    unsigned long long *counter = nullptr;
+    char *stage = nullptr;          // device staging for host-pointer calls
+    size_t stage_bytes = 0;
+    cudaEvent_t last = nullptr;     // completion of the previous launch (serialises calls)
+};
+
+static std::mutex g_mu;
+static DevState g_dev[64];
+
+static int cuda_fail(cudaError_t e) {
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? TW_ENOMEM : TW_ECUDA;
+}
+
+static int dev_state(DevState **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= 64) return TW_ECUDA;
+    DevState &d = g_dev[dev];
+    if (!d.init) {
+        if ((e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaMalloc(&d.counter, 64)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaEventCreateWithFlags(&d.last, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e);
+        d.init = true;
+    }
+    *out = &d;
+    return TW_OK;
+}
+
+static int grow(char **buf, size_t *have, size_t need) {
+    if (*have >= need) return TW_OK;
+    if (*buf) {
+        cudaDeviceSynchronize();
+        cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) { *buf = nullptr; return cuda_fail(e); }
+    *have = need;
+    return TW_OK;
+}
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+static int check_opts(const tw_opts *o) {
+    if (!o) return TW_OK;
+    if (o->precision != TW_PREC_FP64 && o->precision != TW_PREC_MIXED) return TW_EINVAL;
+    const int spi = o->samples_per_iter;
+    if (spi != 32 && spi != 64 && spi != 128) return TW_EINVAL;
+    if (o->max_samples < 64 || o->max_samples > 16384 || o->max_samples < spi) return TW_EINVAL;
+    return TW_OK;
+}
+
+// Launches the contour kernel over src.n positions.  Device pointers only.
+static int launch(DevState &d, const WorkSrc &src, double tol, const tw_opts &o, double *out, double *err,
+                  int32_t *nsamp, int8_t *pstat, cudaStream_t st) {
+    const int spl = o.samples_per_iter / 32;
+    const int cap = (o.max_samples + 63) & ~63;
+    launch_fn lf;
+    occ_fn of;
+    pick_kernel(o.precision, spl, &lf, &of);
+    int occ = 0;
+    cudaError_t e = of(&occ);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (occ < 1) occ = 1;
+    int64_t blocks = (int64_t)d.nsm * occ;
+    const int64_t need_blocks = (src.n + WPB - 1) / WPB;
+    if (blocks > need_blocks) blocks = need_blocks;
+    if (blocks < 1) blocks = 1;
+    const size_t slot_bytes = arena_slot_bytes(cap);
+    int rc = grow(&d.arena, &d.arena_bytes, slot_bytes * (size_t)blocks * WPB);
+    if (rc) return rc;
+    // serialise with the previous launch (the arena and counter are shared)
+    if ((e = cudaStreamWaitEvent(st, d.last, 0)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(d.counter, 0, 5 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_fail(e);
+    KParams kp;
+    kp.src = src;
+    kp.out = out;
+    kp.err = err;
+    kp.nsamp = nsamp;
+    kp.pstat = pstat;
+    kp.arena = d.arena;
+    kp.slot_bytes = slot_bytes;
+    kp.cap = cap;
+    kp.tol = tol;
+    kp.counter = d.counter;
+    if ((e = lf((unsigned)blocks, st, kp)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaEventRecord(d.last, st)) != cudaSuccess) return cuda_fail(e);
+    return TW_OK;
+}
+
+// Runs one call: validates pointer kinds, stages host buffers, launches.
+// ins/insz: input arrays (host or device) and their byte sizes; the staged
+// device copies are handed to `bind`, which fills src from them.
+struct Call {
+    const void *in[4];
+    size_t insz[4];
+    int nin;
+    int64_t n;  // positions (outputs)
+};
+
+template <typename Bind>
+static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *out, Bind bind) {
+    tw_opts o;
+    tw_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (check_opts(&o)) return TW_EINVAL;
+    if (c.n == 0) return TW_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState *dp = nullptr;
+    int rc = dev_state(&dp);
+    if (rc) return rc;
+    DevState &d = *dp;
+    cudaStream_t st = (cudaStream_t)o.stream;
+    // all arrays of a call must be of one kind
+    const bool dev = is_device_ptr(out);
+    for (int i = 0; i < c.nin; i++)
+        if (c.insz[i] && is_device_ptr(c.in[i]) != dev) return TW_EINVAL;
+    if (o.err_out && is_device_ptr(o.err_out) != dev) return TW_EINVAL;
+    if (o.nsamp_out && is_device_ptr(o.nsamp_out) != dev) return TW_EINVAL;
+    if (o.pos_status && is_device_ptr(o.pos_status) != dev) return TW_EINVAL;
+    const void *din[4];
+    if (dev) {
+        for (int i = 0; i < c.nin; i++) din[i] = c.in[i];
+        WorkSrc src = bind(din);
+        return launch(d, src, tol, o, out, o.err_out, o.nsamp_out, o.pos_status, st);
+    }
+    // host pointers: stage inputs and outputs through device memory
+    size_t off[4], total = 0;
+    for (int i = 0; i < c.nin; i++) { off[i] = total; total += align256(c.insz[i]); }
+    const size_t o_out = total; total += align256((size_t)c.n * 8);
+    const size_t o_err = total; total += align256((size_t)c.n * 8);
+    const size_t o_ns = total; total += align256((size_t)c.n * 4);
+    const size_t o_ps = total; total += align256((size_t)c.n);
+    if ((rc = grow(&d.stage, &d.stage_bytes, total))) return rc;
+    cudaError_t e;
+    // the staging buffer is shared: wait for the previous call to finish with it
+    if ((e = cudaStreamWaitEvent(st, d.last, 0)) != cudaSuccess) return cuda_fail(e);
+    for (int i = 0; i < c.nin; i++) {
+        din[i] = d.stage + off[i];
+        if (c.insz[i] && (e = cudaMemcpyAsync(d.stage + off[i], c.in[i], c.insz[i], cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    WorkSrc src = bind(din);
+    double *dout = (double *)(d.stage + o_out);
+    double *derr = o.err_out ? (double *)(d.stage + o_err) : nullptr;
+    int32_t *dns = o.nsamp_out ? (int32_t *)(d.stage + o_ns) : nullptr;
+    int8_t *dps = (int8_t *)(d.stage + o_ps);
+    if ((rc = launch(d, src, tol, o, dout, derr, dns, dps, st))) return rc;
+    int8_t *hps = o.pos_status;
+    int8_t *tmp_ps = nullptr;
+    if (!hps) { tmp_ps = new int8_t[c.n]; hps = tmp_ps; }
+    e = cudaMemcpyAsync(out, dout, (size_t)c.n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && derr) e = cudaMemcpyAsync(o.err_out, derr, (size_t)c.n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && dns) e = cudaMemcpyAsync(o.nsamp_out, dns, (size_t)c.n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hps, dps, (size_t)c.n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int warn = TW_OK;
+    if (e == cudaSuccess)
+        for (int64_t i = 0; i < c.n; i++)
+            if (hps[i] & PS_CAP) { warn = TW_WCAP; break; }
+    delete[] tmp_ps;
+    if (e != cudaSuccess) return cuda_fail(e);
+    return warn;
+}
+
+}  // namespace tw
+
+using namespace tw;
+
+extern "C" {
+
+void tw_opts_default(tw_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = TW_PREC_FP64;
+    o->samples_per_iter = 64;
+    o->max_samples = 4096;
+    o->autotune = 0;
+}
+
+int tw_mag_ex(double s, double q, double rho, const double *y1, const double *y2, int64_t n, double rel_tol,
+              double *out, const tw_opts *opts) {
+    if (n < 0 || !finite_pos(s) || !finite_pos(q) || !finite_pos(rho) || !finite_pos(rel_tol)) return TW_EINVAL;
+    if (n > 0 && (!y1 || !y2 || !out)) return TW_EINVAL;
+    Call c;
+    c.nin = 2;
+    c.in[0] = y1; c.insz[0] = (size_t)n * 8;
+    c.in[1] = y2; c.insz[1] = (size_t)n * 8;
+    c.n = n;
+    return run_call(c, rel_tol, opts, out, [&](const void **din) {
+        WorkSrc w;
+        memset(&w, 0, sizeof(w));
+        w.kind = 0; w.n = n; w.s = s; w.q = q; w.rho = rho;
+        w.y1 = (const double *)din[0];
+        w.y2 = (const double *)din[1];
+        return w;
+    });
+}
+
+int tw_mag(double s, double q, double rho, const double *y1, const double *y2, int64_t n, double rel_tol,
+           double *out) {
+    return tw_mag_ex(s, q, rho, y1, y2, n, rel_tol, out, nullptr);
+}
+
+int tw_lightcurve_ex(double s, double q, double rho, double u0, double alpha, double t0, double tE,
+                     const double *times, int64_t n, double rel_tol, double *out, const tw_opts *opts) {
+    if (n < 0 || !finite_pos(s) || !finite_pos(q) || !finite_pos(rho) || !finite_pos(rel_tol) || !finite_pos(tE) ||
+        !isfinite(u0) || !isfinite(alpha) || !isfinite(t0))
+        return TW_EINVAL;
+    if (n > 0 && (!times || !out)) return TW_EINVAL;
+    Call c;
+    c.nin = 1;
+    c.in[0] = times; c.insz[0] = (size_t)n * 8;
+    c.n = n;
+    return run_call(c, rel_tol, opts, out, [&](const void **din) {
+        WorkSrc w;
+        memset(&w, 0, sizeof(w));
+        w.kind = 1; w.n = n; w.s = s; w.q = q; w.rho = rho;
+        w.u0 = u0; w.alpha = alpha; w.t0 = t0; w.tE = tE;
+        w.times = (const double *)din[0];
+        return w;
+    });
+}
+
+int tw_lightcurve(double s, double q, double rho, double u0, double alpha, double t0, double tE,
+                  const double *times, int64_t n, double rel_tol, double *out) {
+    return tw_lightcurve_ex(s, q, rho, u0, alpha, t0, tE, times, n, rel_tol, out, nullptr);
+}
+
+int tw_lightcurve_batch(const double *params, const int64_t *offsets, const double *times, int64_t ncurve,
+                        double rel_tol, double *out, const tw_opts *opts) {
+    if (ncurve < 0 || !finite_pos(rel_tol)) return TW_EINVAL;
+    if (ncurve == 0) return TW_OK;
+    if (!params || !offsets) return TW_EINVAL;
+    // the total length is needed on the host: read offsets[ncurve]
+    int64_t total = 0;
+    if (is_device_ptr(offsets)) {
+        if (cudaMemcpy(&total, offsets + ncurve, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+    } else {
+        if (offsets[0] != 0) return TW_EINVAL;
+        for (int64_t k = 0; k < ncurve; k++)
+            if (offsets[k + 1] < offsets[k]) return TW_EINVAL;
+        total = offsets[ncurve];
+    }
+    if (total < 0) return TW_EINVAL;
+    if (total > 0 && (!times || !out)) return TW_EINVAL;
+    Call c;
+    c.nin = 3;
+    c.in[0] = params; c.insz[0] = (size_t)ncurve * 7 * 8;
+    c.in[1] = offsets; c.insz[1] = (size_t)(ncurve + 1) * 8;
+    c.in[2] = times; c.insz[2] = (size_t)total * 8;
+    c.n = total;
+    return run_call(c, rel_tol, opts, out, [&](const void **din) {
+        WorkSrc w;
+        memset(&w, 0, sizeof(w));
+        w.kind = 2; w.n = total;
+        w.params = (const double *)din[0];
+        w.offsets = (const int64_t *)din[1];
+        w.times = (const double *)din[2];
+        w.ncurve = ncurve;
+        return w;
+    });
+}
+
+const char *tw_status_str(int code) {
+    switch (code) {
+        case TW_OK: return "ok";
+        case TW_EINVAL: return "invalid argument";
+        case TW_ECUDA: return "CUDA runtime error";
+        case TW_ENOMEM: return "out of device memory";
+        case TW_ETIMEOUT: return "device-side wait timed out";
+        case TW_WCAP: return "sample cap reached for at least one position";
+        default: break;
+    }
+    return "unknown status";
+}
+
+int tw_version(void) { return 100; }
+
+int tw_last_launch_work(int64_t out[4]) {
+    if (!out) return TW_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState *dp = nullptr;
+    int rc = dev_state(&dp);
+    if (rc) return rc;
+    cudaError_t e = cudaEventSynchronize(dp->last);
+    unsigned long long h[5];
+    if (e == cudaSuccess) e = cudaMemcpy(h, dp->counter, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int i = 0; i < 4; i++) out[i] = (int64_t)h[i + 1];
+    return TW_OK;
+}
+
+}  // extern "C"

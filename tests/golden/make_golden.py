@@ -1,0 +1,142 @@
+"""Writes the stored expected values of the GPU parity tests.
+
+Every value here is computed by the CPU oracle (``oracle/``) from inputs drawn
+by ``paper_2501_03322_gb300.workloads`` (seeded grids and random draws, no lens
+arithmetic).  Run from the repository root:
+
+    python tests/golden/make_golden.py [name ...]
+
+Files (text, one position per line: inputs, mu, oracle status):
+  lightcurve_central.txt  all 1000 points of the central-caustic light curve
+  map_planetary.txt       256 sampled cells of the 512 x 512 planetary-caustic map
+  stress_resonant.txt     200 sampled positions of the resonant large-source set
+  batch_lightcurves.txt   192 sampled (curve, time) points of the 4096-curve batch
+  paper_worked.txt        the paper's worked configurations (Fig. 1, 2, 5)
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+from paper_2501_03322_gb300 import workloads as W  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _write(name, header, cols, rows):
+    rows = list(rows)
+    path = os.path.join(HERE, name)
+    with open(path, "w") as f:
+        for line in header.strip().splitlines():
+            f.write("# " + line + "\n")
+        f.write("# columns: " + " ".join(cols) + "\n")
+        for r in rows:
+            f.write(" ".join(repr(float(v)) if isinstance(v, (float, np.floating)) else str(int(v)) for v in r) + "\n")
+    print("wrote", path, len(rows), "rows")
+
+
+def lightcurve_central():
+    c = W.LIGHTCURVE_CENTRAL
+    t = W.lightcurve_central_times(c["n"])
+    mu, st, nx = O.lightcurve(c["s"], c["q"], c["rho"], c["u0"], c["alpha"], c["t0"], c["tE"], t, scan_K=256)
+    hdr = ("Central-caustic light curve: s=1, q=1e-3, rho=1e-3, u0=0.01, alpha=1 rad, t0=0, tE=20 d,\n"
+           "1000 times linspace(-1, 1); oracle magnifications (binary128 linking-free contour integral).")
+    _write("lightcurve_central.txt", hdr, ["t", "mu", "status", "ncross"], zip(t, mu, st, nx))
+
+
+def map_planetary():
+    c = W.MAP_PLANETARY
+    y1, y2 = W.map_grid()
+    idx = W.sample_indices(y1.size, 256, seed=101)
+    mu, st, nx = O.mag(c["s"], c["q"], c["rho"], y1[idx], y2[idx], scan_K=256)
+    hdr = ("Planetary-caustic map: s=0.8, q=1e-4, rho=5e-4, 512x512 cell centres of the 0.1x0.1 box centred\n"
+           "on (-0.44985, 0.016993); 256 cells sampled with seed 101; oracle magnifications.")
+    _write("map_planetary.txt", hdr, ["index", "y1", "y2", "mu", "status", "ncross"], zip(idx, y1[idx], y2[idx], mu, st, nx))
+
+
+def stress_resonant():
+    c = W.STRESS_RESONANT
+    y1, y2 = W.stress_positions()
+    idx = W.sample_indices(y1.size, 200, seed=202)
+    mu, st, nx = O.mag(c["s"], c["q"], c["rho"], y1[idx], y2[idx], scan_K=256)
+    hdr = ("Resonant large source: s=1, q=0.5, rho=0.05, 1e6 positions uniform in |y|<0.6 (seed 2);\n"
+           "200 sampled with seed 202; oracle magnifications.")
+    _write("stress_resonant.txt", hdr, ["index", "y1", "y2", "mu", "status", "ncross"], zip(idx, y1[idx], y2[idx], mu, st, nx))
+
+
+def batch_lightcurves():
+    params, offsets, times = W.batch_lightcurves()
+    rng = np.random.default_rng(303)
+    curves = np.sort(rng.choice(params.shape[0], 64, replace=False))
+    jobs = []
+    for k in curves:
+        n_k = offsets[k + 1] - offsets[k]
+        pick = np.sort(rng.choice(n_k, 3, replace=False)) + offsets[k]
+        jobs.append((k, pick))
+
+    def run(job):
+        k, pick = job
+        s, q, rho, u0, alpha, t0, tE = params[k]
+        mu, st, nx = O.lightcurve(s, q, rho, u0, alpha, t0, tE, times[pick], scan_K=256, nthreads=1)
+        return [(k, i, times[i], m, a, b) for i, m, a, b in zip(pick, mu, st, nx)]
+
+    rows = []
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
+        for r in ex.map(run, jobs):
+            rows.extend(r)
+    hdr = ("Batch of 4096 light curves (workloads.batch_lightcurves, seed 0); 64 curves x 3 times sampled\n"
+           "with seed 303; oracle magnifications.")
+    _write("batch_lightcurves.txt", hdr, ["curve", "index", "t", "mu", "status", "ncross"], rows)
+
+
+def paper_worked():
+    rows = []
+    # Fig. 1 (Sec. 2.2): s=0.5, q=1e-6, rho=1e-4, source centre -1.49981640625 + 0.0035i (limb near a cusp
+    # of the planetary caustic)
+    cases = [("fig1", 0.5, 1e-6, 1e-4, -1.49981640625, 0.0035)]
+    # Fig. 2 (Sec. 2.3): s=1, q=0.1, rho=0.1, centre 0.2+0.2i (two caustic crossings)
+    cases.append(("fig2", 1.0, 0.1, 0.1, 0.2, 0.2))
+    # Fig. 5 (Sec. 4.2): s=0.5, q=1e-6, rho=1e-4, horizontal line y2 = -0.0035 near the planetary caustic;
+    # the two positions where the paper reports spikes of another code, and a line across the caustic
+    cases.append(("fig5_spike_a", 0.5, 1e-6, 1e-4, -1.49998960, -0.0035))
+    cases.append(("fig5_spike_b", 0.5, 1e-6, 1e-4, -1.49993410, -0.0035))
+    for x in np.linspace(-1.50012, -1.49988, 25):
+        cases.append(("fig5_line", 0.5, 1e-6, 1e-4, float(x), -0.0035))
+
+    def run(c):
+        tag, s, q, rho, y1, y2 = c
+        mu, st, nx = O.mag(s, q, rho, [y1], [y2], scan_K=512, nthreads=1)
+        return (tag, s, q, rho, y1, y2, mu[0], st[0], nx[0])
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
+        out = list(ex.map(run, cases))
+    path = os.path.join(HERE, "paper_worked.txt")
+    with open(path, "w") as f:
+        f.write("# The paper's worked configurations (it prints no magnification values for them):\n")
+        f.write("#   fig1: Sec. 2.2, Fig. 1 (coefficient accuracy, limb next to a planetary-caustic cusp)\n")
+        f.write("#   fig2: Sec. 2.3, Fig. 2 (two caustic crossings, three full images and two broken tracks)\n")
+        f.write("#   fig5_*: Sec. 4.2, Fig. 5 (low-q light curve at y2=-0.0035; spike positions of another code)\n")
+        f.write("# Values: CPU oracle magnifications.\n")
+        f.write("# columns: tag s q rho y1 y2 mu status ncross\n")
+        for r in out:
+            f.write("%s %r %r %r %r %r %r %d %d\n" % (r[0], r[1], r[2], r[3], r[4], r[5], float(r[6]), int(r[7]), int(r[8])))
+    print("wrote", path, len(out), "rows")
+
+
+ALL = {"lightcurve_central": lightcurve_central, "map_planetary": map_planetary, "stress_resonant": stress_resonant,
+       "batch_lightcurves": batch_lightcurves, "paper_worked": paper_worked}
+
+if __name__ == "__main__":
+    names = sys.argv[1:] or list(ALL)
+    for nm in names:
+        t = time.time()
+        ALL[nm]()
+        print(nm, "%.1fs" % (time.time() - t))

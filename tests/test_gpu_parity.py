@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA contour integrator against the CPU oracle.
+
+Expected values are the oracle's, stored under tests/golden/ by
+tests/golden/make_golden.py (written only by the oracle from the seeded
+workload generators).  The bar is the relative magnification error 1e-4 that
+the method targets (rel_tol = 1e-4, Sec. 4.1).  Full-size workloads run in the
+benchmark's launch configuration and are compared on sampled positions.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2501_03322_gb300 as P  # noqa: E402
+from paper_2501_03322_gb300 import workloads as W  # noqa: E402
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TOL = 1e-4
+MODES = [P.PREC_FP64, P.PREC_MIXED]
+
+
+def load(name):
+    rows = [ln.split() for ln in open(os.path.join(GOLD, name)) if not ln.startswith("#") and ln.strip()]
+    return rows
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def rel_err(got, ref):
+    return np.abs(np.asarray(got) / np.asarray(ref) - 1.0)
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_lightcurve_central_all_points(prec):
+    c = W.LIGHTCURVE_CENTRAL
+    rows = load("lightcurve_central.txt")
+    t = np.array([float(r[0]) for r in rows])
+    ref = np.array([float(r[1]) for r in rows])
+    ok = np.array([int(r[2]) == 0 for r in rows])
+    mu, err, ns, st = P.lightcurve(c["s"], c["q"], c["rho"], c["u0"], c["alpha"], c["t0"], c["tE"], dev(t),
+                                   rel_tol=c["rel_tol"], precision=prec, details=True)
+    torch.cuda.synchronize()
+    mu = mu.cpu().numpy()
+    e = rel_err(mu[ok], ref[ok])
+    assert ok.sum() >= 990
+    assert e.max() <= TOL, (e.max(), t[ok][np.argmax(e)])
+    assert (st.cpu().numpy() & (P.POS_IMAGECOUNT | P.POS_NONFINITE)).sum() == 0
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_map_planetary_full_grid_sampled(prec):
+    c = W.MAP_PLANETARY
+    y1, y2 = W.map_grid()
+    mu = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(y2), rel_tol=c["rel_tol"], precision=prec)
+    torch.cuda.synchronize()
+    mu = mu.cpu().numpy()
+    assert np.isfinite(mu).all() and (mu >= 1.0 - TOL).all()
+    rows = load("map_planetary.txt")
+    idx = np.array([int(r[0]) for r in rows])
+    ref = np.array([float(r[3]) for r in rows])
+    ok = np.array([int(r[4]) == 0 for r in rows])
+    e = rel_err(mu[idx][ok], ref[ok])
+    assert e.max() <= TOL, (e.max(), idx[ok][np.argmax(e)])
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_paper_worked_configurations(prec):
+    rows = load("paper_worked.txt")
+    for r in rows:
+        tag, s, q, rho, y1, y2, ref, st = r[0], *map(float, r[1:7]), int(r[7])
+        if st != 0:
+            continue
+        mu = P.mag(s, q, rho, dev([y1]), dev([y2]), rel_tol=TOL, precision=prec)
+        got = float(mu.cpu()[0])
+        assert abs(got / ref - 1) <= TOL, (tag, y1, y2, got, ref)
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_stress_resonant_sampled(prec):
+    c = W.STRESS_RESONANT
+    rows = load("stress_resonant.txt")
+    y1 = np.array([float(r[1]) for r in rows])
+    y2 = np.array([float(r[2]) for r in rows])
+    ref = np.array([float(r[3]) for r in rows])
+    ok = np.array([int(r[4]) == 0 for r in rows])
+    mu = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(y2), rel_tol=c["rel_tol"], precision=prec).cpu().numpy()
+    e = rel_err(mu[ok], ref[ok])
+    assert e.max() <= TOL, (e.max(), np.argmax(e))
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_batch_lightcurves_sampled(prec):
+    params, offsets, times = W.batch_lightcurves()
+    rows = load("batch_lightcurves.txt")
+    idx = np.array([int(r[1]) for r in rows])
+    ref = np.array([float(r[3]) for r in rows])
+    ok = np.array([int(r[4]) == 0 for r in rows])
+    mu = P.lightcurve_batch(torch.as_tensor(params, device="cuda"), torch.as_tensor(offsets, device="cuda"),
+                            dev(times), rel_tol=1e-4, precision=prec)
+    torch.cuda.synchronize()
+    mu = mu.cpu().numpy()
+    assert np.isfinite(mu).all()
+    e = rel_err(mu[idx][ok], ref[ok])
+    assert e.max() <= TOL, (e.max(), idx[ok][np.argmax(e)])
+
+
+def test_host_and_device_pointers_agree():
+    c = W.LIGHTCURVE_CENTRAL
+    t = W.lightcurve_central_times(97)  # ragged size
+    a = P.lightcurve(c["s"], c["q"], c["rho"], c["u0"], c["alpha"], c["t0"], c["tE"], t)
+    b = P.lightcurve(c["s"], c["q"], c["rho"], c["u0"], c["alpha"], c["t0"], c["tE"], dev(t)).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+
+
+def test_edge_cases():
+    # one position; non-finite positions give NaN and the non-finite status, the others are unaffected
+    y1 = np.array([0.3, np.nan, 0.1, np.inf])
+    y2 = np.array([0.1, 0.0, np.nan, 0.0])
+    mu, err, ns, st = P.mag(1.0, 1e-3, 1e-3, y1, y2, details=True)
+    assert np.isfinite(mu[0]) and np.isnan(mu[1:]).all()
+    assert (st[1:] & P.POS_NONFINITE).all() and st[0] == 0
+    # a tiny cap still returns a finite estimate and flags the cap
+    mu, err, ns, st = P.mag(1.0, 0.5, 0.05, np.array([0.0]), np.array([0.04]), rel_tol=1e-9, max_samples=128,
+                            details=True)
+    assert np.isfinite(mu[0]) and (st[0] & P.POS_CAP) and ns[0] <= 128
+    # very large source: mu -> 1; centred on a near point lens: sqrt(1 + 4/rho^2)
+    mu = P.mag(1.0, 0.3, 40.0, np.array([0.0]), np.array([0.0]))
+    assert 1.0 < mu[0] < 1.003
+    s, q = 10.0, 1e-9
+    mu = P.mag(s, q, 0.1, np.array([-q * s / (1 + q)]), np.array([0.0]))
+    assert abs(mu[0] / np.sqrt(1 + 4 / 0.01) - 1) < TOL
+
+
+@pytest.mark.parametrize("spi", [32, 128])
+def test_samples_per_iteration_variants(spi):
+    c = W.LIGHTCURVE_CENTRAL
+    rows = load("lightcurve_central.txt")[::7]
+    t = np.array([float(r[0]) for r in rows])
+    ref = np.array([float(r[1]) for r in rows])
+    ok = np.array([int(r[2]) == 0 for r in rows])
+    mu = P.lightcurve(c["s"], c["q"], c["rho"], c["u0"], c["alpha"], c["t0"], c["tE"], t, samples_per_iter=spi)
+    assert rel_err(mu[ok], ref[ok]).max() <= TOL
+
+
+def test_mirror_and_mass_swap_symmetry_full_size():
+    """Properties that hold at any size: mu(y1, y2) = mu(y1, -y2) and
+    mu(s, q, y1, y2) = mu(s, 1/q, -y1, y2), on the full planetary map."""
+    c = W.MAP_PLANETARY
+    y1, y2 = W.map_grid()
+    a = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(y2)).cpu().numpy()
+    b = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(-y2)).cpu().numpy()
+    d = P.mag(c["s"], 1.0 / c["q"], c["rho"], dev(-y1), dev(y2)).cpu().numpy()
+    assert rel_err(a, b).max() <= 2 * TOL
+    assert rel_err(a, d).max() <= 2 * TOL
