@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 #   one limb sample outside the sweeps: limb point (8), Eq. 6 coefficients
 #     (~100), residual/Jacobian/f'/f'' per root (68 -> 340), dz/dtheta and
 #     z' ^ z'' per root (29 -> 145): ~600 (FP64)
-#   mixed mode adds one FP64 Newton step per root per sample (5 x 94 = 470)
+#   one FP64 Newton pass over the five roots (mixed mode): 5 x 94 = 470
 #   one edge: image linking distances and 3-5 links of trapezium + parabolic
 #     correction + four error terms: ~145 (FP64), ~20 (FP32)
 F_SWEEP = 760.0
@@ -165,9 +165,8 @@ class ClockSampler:
 
 
 def flops_of(work, mode):
-    f64 = (F_SAMPLE64 * work["samples"] + F_SWEEP * work["sweeps64"] + F_EDGE64 * work["edges"])
-    if mode == "mixed":
-        f64 += F_NEWTON64 * work["samples"]
+    f64 = (F_SAMPLE64 * work["samples"] + F_SWEEP * work["sweeps64"] + F_EDGE64 * work["edges"]
+           + F_NEWTON64 * work["newton64"])
     f32 = F_SWEEP * work["sweeps32"] + F_EDGE32 * work["edges"]
     return f64, f32
 
@@ -229,11 +228,18 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=128, help="positions in the CPU oracle baseline sample")
     ap.add_argument("--ref-sample", type=int, default=24, help="positions per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--limit", type=int, default=0,
+                    help="use a seeded sub-sample of this many positions (small profiling captures)")
     args = ap.parse_args()
 
     metric = "finite-source mags/sec at rel.err<=1e-4: surrogate+fallback vs plain, 1 GB300"
     unit = "mags/s"
     wl = workload(args.workload)
+    if args.limit and wl["kind"] == "mag" and args.limit < wl["n"]:
+        from paper_2501_03322_gb300 import workloads as W
+
+        idx = W.sample_indices(wl["n"], args.limit, seed=4242)
+        wl.update(y1=wl["y1"][idx], y2=wl["y2"][idx], n=idx.size, name=wl["name"] + "_sub%d" % idx.size)
     cfg = config_of(wl, args.mode, args.gpus)
     if args.impl == "reference":
         run_reference(args, wl, cfg, metric, unit)
@@ -288,6 +294,7 @@ def main():
     sampler = ClockSampler(local)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     f64 = f32 = 0.0
+    work = dict(samples=0, sweeps64=0, sweeps32=0, edges=0, newton64=0)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -300,6 +307,8 @@ def main():
         evs[i][1].record(stream)
         evs[i][1].synchronize()
         w = P.last_launch_work()
+        for k in work:
+            work[k] += w[k]
         a, b = flops_of(w, args.mode)
         f64 += a
         f32 += b
@@ -375,7 +384,12 @@ def main():
             "config": cfg, "roofline": roof, "clocks": clocks,
             "e2e": {"value": world * wl["n"] / t_e2e, "unit": unit, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps, "wall_s_timed": wall}
+            "gpu_launches": args.steps, "wall_s_timed": wall,
+            "work": {"samples_per_position": work["samples"] / (args.steps * wl["n"]),
+                     "fp64_sweeps_per_sample": work["sweeps64"] / max(work["samples"], 1),
+                     "fp32_sweeps_per_sample": work["sweeps32"] / max(work["samples"], 1),
+                     "fp64_newton_per_sample": work["newton64"] / max(work["samples"], 1),
+                     "edges_per_sample": work["edges"] / max(work["samples"], 1)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, cores = cpu_oracle_sample(wl, args.cpu_sample)
         line["cpu_baseline"] = {"value": n / dt, "unit": unit, "cores": cores, "kind": "oracle",

@@ -127,10 +127,18 @@ int tw_version(void);
 
 /* Work done by the most recent launch on the current device (waits for it):
  * out[0] limb samples, out[1] FP64 Aberth sweeps (five roots each), out[2]
- * FP32 Aberth sweeps, out[3] edge evaluations (image linking + area + error).
+ * FP32 Aberth sweeps, out[3] edge evaluations (image linking + area + error),
+ * out[4] FP64 Newton passes over the five roots (mixed precision).
  * These are the units of the FLOP accounting of the roofline report; the
  * paper has no counterpart (it reports no operation counts). */
-int tw_last_launch_work(int64_t out[4]);
+int tw_last_launch_work(int64_t out[5]);
+
+/* Device self-test of the library's FP64 reciprocal (the hardware
+ * approximation refined by two Newton-Raphson steps, used for every complex
+ * division of the kernels) against IEEE division, over 2^20 values of
+ * magnitude 1e-300..1e300: *rcp_max_rel_err receives the largest relative
+ * difference.  Synchronous.  The paper has no counterpart. */
+int tw_selftest(double *rcp_max_rel_err);
 
 #ifdef __cplusplus
 }

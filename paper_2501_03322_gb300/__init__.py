@@ -84,6 +84,8 @@ def lib():
             L.tw_version.restype = I
             L.tw_last_launch_work.argtypes = [P]
             L.tw_last_launch_work.restype = I
+            L.tw_selftest.argtypes = [P]
+            L.tw_selftest.restype = I
             _lib = L
     return _lib
 
@@ -155,10 +157,17 @@ def _prep(arr):
 
 
 def last_launch_work() -> dict:
-    """Samples, FP64/FP32 Aberth sweeps and edge evaluations of the last launch."""
-    a = np.zeros(4, np.int64)
+    """Samples, FP64/FP32 Aberth sweeps, edge evaluations and FP64 Newton passes of the last launch."""
+    a = np.zeros(5, np.int64)
     _check(lib().tw_last_launch_work(a.ctypes.data_as(ctypes.c_void_p)))
-    return dict(samples=int(a[0]), sweeps64=int(a[1]), sweeps32=int(a[2]), edges=int(a[3]))
+    return dict(samples=int(a[0]), sweeps64=int(a[1]), sweeps32=int(a[2]), edges=int(a[3]), newton64=int(a[4]))
+
+
+def selftest_rcp() -> float:
+    """Largest relative error of the device FP64 reciprocal against IEEE division."""
+    v = ctypes.c_double(0.0)
+    _check(lib().tw_selftest(ctypes.byref(v)))
+    return v.value
 
 
 def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64, max_samples=4096,

@@ -41,8 +41,8 @@ enum : int { PS_CAP = 1, PS_IMAGECOUNT = 2, PS_NONFINITE = 4, PS_SOLVER = 8 };
 struct Arena {
     double *theta;
     cxd *roots;  // [slot*5 + i]
-    cxd *zp;     // [slot*5 + i]
-    double *w;   // [slot*5 + i]
+    cxf *zp;     // [slot*5 + i]
+    float *w;    // [slot*5 + i]
     uint32_t *meta;
     double *eA;
     double *eE;
@@ -56,7 +56,7 @@ __host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size
 // Bytes of one warp slot for a sample cap `cap`.
 __host__ __device__ inline size_t arena_slot_bytes(int cap) {
     size_t c = (size_t)cap;
-    return align256(c * 8) + align256(c * 5 * 16) * 2 + align256(c * 5 * 8) + align256(c * 4) +
+    return align256(c * 8) + align256(c * 5 * 16) + align256(c * 5 * 8) + align256(c * 5 * 4) + align256(c * 4) +
            align256(c * 8) * 2 + align256(c * 2) * 2 + align256(c * 8);
 }
 
@@ -66,8 +66,8 @@ __device__ inline Arena arena_at(char *base, size_t slot_bytes, int cap, int slo
     Arena a;
     a.theta = (double *)p; p += align256(c * 8);
     a.roots = (cxd *)p; p += align256(c * 5 * 16);
-    a.zp = (cxd *)p; p += align256(c * 5 * 16);
-    a.w = (double *)p; p += align256(c * 5 * 8);
+    a.zp = (cxf *)p; p += align256(c * 5 * 8);
+    a.w = (float *)p; p += align256(c * 5 * 4);
     a.meta = (uint32_t *)p; p += align256(c * 4);
     a.eA = (double *)p; p += align256(c * 8);
     a.eE = (double *)p; p += align256(c * 8);
@@ -78,8 +78,9 @@ __device__ inline Arena arena_at(char *base, size_t slot_bytes, int cap, int slo
 }
 
 struct Img {
-    cxd z, zp;
-    double w;
+    cxd z;   // image position (FP64: the trapezium terms need it)
+    cxf zp;  // dz/dtheta
+    float w; // z' ^ z''
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -89,22 +90,23 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Normal link of image a (angle theta) to image b (theta + dth) of parity sgn:
-// trapezium (Eq. 9) plus the mean of the two parabolic corrections (Eq. 10),
-// and the error terms E1..E4 of Eq. 17.
-__device__ __forceinline__ void link_contrib(const Img &a, const Img &b, double sgn, double dth, double &dA,
-                                             double &dE) {
-    const double d2 = dth * dth, d3 = d2 * dth;
+// trapezium (Eq. 9, FP64) plus the mean of the two parabolic corrections
+// (Eq. 10), and the error terms E1..E4 of Eq. 17 (FP32: corrections are many
+// orders below the area and only need relative accuracy).
+__device__ __forceinline__ void link_contrib(const Img &a, const Img &b, double sgn, float dth, double &dA,
+                                             float &dE) {
+    const float d2 = dth * dth, d3 = d2 * dth;
     const double At = 0.5 * wedge(a.z, b.z);
-    const double p1 = (a.w + b.w) * d3 * (1.0 / 24.0);
-    const cxd dz = b.z - a.z, dzp = b.zp - a.zp;
-    const double p2 = wedge(dz, dzp) * dth * (1.0 / 12.0);
-    const double Ap = 0.5 * (p1 + p2);
-    dA += sgn * (At + Ap);
-    const double e1 = fabs(a.w - b.w) * d3 * (1.0 / 48.0);
-    const double dt = fabs(dot(a.zp, b.zp));
-    const double e2 = 1.5 * fabs(Ap * (norm2(dz) * rcp(fmax(d2 * dt, 1e-300)) - 1.0));
-    const double e3 = 0.1 * fabs(Ap) * d2;
-    const double e4 = fabs(p1 - p2);
+    const float p1 = (a.w + b.w) * d3 * (1.0f / 24.0f);
+    const cxf dz = to_f(b.z - a.z), dzp = b.zp - a.zp;
+    const float p2 = wedge(dz, dzp) * dth * (1.0f / 12.0f);
+    const float Ap = 0.5f * (p1 + p2);
+    dA += sgn * (At + (double)Ap);
+    const float e1 = fabsf(a.w - b.w) * d3 * (1.0f / 48.0f);
+    const float dt = fabsf(dot(a.zp, b.zp));
+    const float e2 = 1.5f * fabsf(Ap * (norm2(dz) / fmaxf(d2 * dt, 1e-37f) - 1.0f));
+    const float e3 = 0.1f * fabsf(Ap) * d2;
+    const float e4 = fabsf(p1 - p2);
     dE += e1 + e2 + e3 + e4;
 }
 
@@ -113,23 +115,23 @@ __device__ __forceinline__ void link_contrib(const Img &a, const Img &b, double 
 // track (M -> P when the pair is created towards +theta, P -> M when it is
 // destroyed) plus the cross-caustic correction of Eq. 11 and its errors
 // (Eq. 18; the sign inside E2 is - for a creation).  dth is the edge's step.
-__device__ __forceinline__ void pair_contrib(const Img &P, const Img &M, bool creation, double dth, double &dA,
-                                             double &dE) {
-    const cxd dz = P.z - M.z;
-    const double adz = sqrt(norm2(dz));
-    const double dt = fabs(dot(P.zp, M.zp));
-    double tt = (dt > 0.0) ? adz * rsqrt(dt) : 4.0 * dth;  // Eq. 11: |z+ - z-| / sqrt|z'+ . z'-|
-    tt = fmin(tt, 4.0 * dth);
-    const double t3 = tt * tt * tt;
-    const double Ap = (P.w - M.w) * t3 * (1.0 / 24.0);
+__device__ __forceinline__ void pair_contrib(const Img &P, const Img &M, bool creation, float dth, double &dA,
+                                             float &dE) {
+    const cxf dz = to_f(P.z - M.z);
+    const float adz = sqrtf(norm2(dz));
+    const float dt = fabsf(dot(P.zp, M.zp));
+    float tt = (dt > 0.0f) ? adz * rsqrtf(dt) : 4.0f * dth;  // Eq. 11: |z+ - z-| / sqrt|z'+ . z'-|
+    tt = fminf(tt, 4.0f * dth);
+    const float t3 = tt * tt * tt;
+    const float Ap = (P.w - M.w) * t3 * (1.0f / 24.0f);
     const double At = creation ? 0.5 * wedge(M.z, P.z) : 0.5 * wedge(P.z, M.z);
-    dA += At + Ap;
-    const double e1 = fabs(P.w + M.w) * t3 * (1.0 / 48.0);
-    const cxd dzp = P.zp - M.zp;
-    const double proj = dot(dz, dzp);
-    const double sq = 2.0 * adz * sqrt(dt);
-    const double e2 = 1.5 * fabs(creation ? proj - sq : proj + sq) * tt;
-    const double e3 = 0.1 * fabs(Ap) * dth * dth;
+    dA += At + (double)Ap;
+    const float e1 = fabsf(P.w + M.w) * t3 * (1.0f / 48.0f);
+    const cxf dzp = P.zp - M.zp;
+    const float proj = dot(dz, dzp);
+    const float sq = 2.0f * adz * sqrtf(dt);
+    const float e2 = 1.5f * fabsf(creation ? proj - sq : proj + sq) * tt;
+    const float e3 = 0.1f * fabsf(Ap) * dth * dth;
     dE += e1 + e2 + e3;
 }
 
@@ -151,7 +153,7 @@ __device__ __forceinline__ constexpr int perm_at(int p, int i) {
 // distance is minimal (Sec. 2.3; ties go to the lowest permutation).  The one
 // image left over when NX != NY is returned in `left`.
 template <int NX, int NY>
-__device__ __forceinline__ void link_class(const Img *X, const Img *Y, double sgn, double dth, double &dA, double &dE,
+__device__ __forceinline__ void link_class(const Img *X, const Img *Y, double sgn, float dth, double &dA, float &dE,
                                            Img &left) {
     constexpr int N = NX > NY ? NX : NY;
     constexpr int M = NX > NY ? NY : NX;
@@ -164,8 +166,8 @@ __device__ __forceinline__ void link_class(const Img *X, const Img *Y, double sg
 #pragma unroll
         for (int i = 0; i < M; i++) {
             const int j = perm_at<N>(p, i);
-            const cxd d = (NX <= NY) ? (Y[j].z - X[i].z) : (Y[i].z - X[j].z);
-            cost += sqrtf((float)norm2(d));
+            const cxf d = to_f((NX <= NY) ? (Y[j].z - X[i].z) : (Y[i].z - X[j].z));
+            cost += sqrtf(norm2(d));
         }
         if (cost < best_cost) { best_cost = cost; best = p; }
     }
@@ -185,7 +187,7 @@ __device__ __forceinline__ void link_class(const Img *X, const Img *Y, double sg
 }
 
 template <int NA, int NB>
-__device__ __forceinline__ void edge_case(const Img *IA, const Img *IB, double dth, double &dA, double &dE) {
+__device__ __forceinline__ void edge_case(const Img *IA, const Img *IB, float dth, double &dA, float &dE) {
     constexpr int PA = (NA - 1) / 2, PB = (NB - 1) / 2;
     Img lp, ln;
     link_class<PA, PB>(IA, IB, 1.0, dth, dA, dE, lp);
@@ -210,23 +212,51 @@ static __device__ __noinline__ void compute_edge(const Arena &ar, int sa, int sb
             IB[k].z = ar.roots[i]; IB[k].zp = ar.zp[i]; IB[k].w = ar.w[i];
         }
     }
-    double dA = 0.0, dE = 0.0;
-    if (na == 3 && nb == 3) edge_case<3, 3>(IA, IB, dth, dA, dE);
-    else if (na == 5 && nb == 5) edge_case<5, 5>(IA, IB, dth, dA, dE);
-    else if (na == 3) edge_case<3, 5>(IA, IB, dth, dA, dE);
-    else edge_case<5, 3>(IA, IB, dth, dA, dE);
+    double dA = 0.0;
+    float dE = 0.0f;
+    const float dthf = (float)dth;
+    if (na == 3 && nb == 3) edge_case<3, 3>(IA, IB, dthf, dA, dE);
+    else if (na == 5 && nb == 5) edge_case<5, 5>(IA, IB, dthf, dA, dE);
+    else if (na == 3) edge_case<3, 5>(IA, IB, dthf, dA, dE);
+    else edge_case<5, 3>(IA, IB, dthf, dA, dE);
+    double dEd = (double)dE;
     // a sample that failed the image-count check: keep refining around it
-    if ((ma | mb) >> 31) dE += fabs(dA);
+    if ((ma | mb) >> 31) dEd += fabs(dA);
     *outA = dA;
-    *outE = dE;
+    *outE = dEd;
 }
 
 // One limb sample: coefficients, roots (warm-started from z), classification,
 // derivatives, stored in slot `slot`.  Returns the sample's status bits.
 // Work done by one warp on one position (for FLOP accounting).
 struct WorkCount {
-    int sw64 = 0, sw32 = 0, edges = 0;
+    int sw64 = 0, sw32 = 0, edges = 0, nw64 = 0;
 };
+
+// First-order warm start: each real image (bit i of `mask`) is moved by dz_i
+// when that step is small against its distance to the nearest other root
+// (far from a critical curve, where the linear prediction holds).
+__device__ __forceinline__ void predict_roots(cxd z[5], const cxf dz[5], unsigned mask) {
+    cxf zf[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) zf[i] = to_f(z[i]);
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        if (!((mask >> i) & 1u)) continue;
+        float sep2 = 3.0e38f;
+#pragma unroll
+        for (int j = 0; j < 5; j++)
+            if (j != i) sep2 = fminf(sep2, norm2(zf[i] - zf[j]));
+        if (norm2(dz[i]) < 0.04f * sep2) z[i] = z[i] + to_d(dz[i]);
+    }
+}
+
+__device__ __forceinline__ unsigned real_mask(uint32_t meta) {
+    unsigned m = 0;
+    const int n = meta_count(meta);
+    for (int k = 0; k < n; k++) m |= 1u << meta_index(meta, k);
+    return m;
+}
 
 template <int PREC>
 __device__ __forceinline__ int limb_sample(const LensK &L, double th, cxd z[5], const Arena &ar, int slot,
@@ -237,8 +267,9 @@ __device__ __forceinline__ int limb_sample(const LensK &L, double th, cxd z[5], 
     const cxd dzeta = {-L.rho * sn, L.rho * cs}; // zeta' = i rho e^{i theta}
     cxd c[6];
     eq6_coeffs(L.s, L.m2, y, c);
+    if (!roots_finite(z)) initial_roots(L.s, y, z);
     float dpa[5];
-    int f = solve_quintic<PREC>(c, z, dpa, 60, wc.sw64, wc.sw32);
+    int f = solve_quintic<PREC>(c, z, dpa, 60, wc.sw64, wc.sw32, wc.nw64);
     SampleRefs o = {&ar.theta[slot], &ar.roots[slot * 5], &ar.zp[slot * 5], &ar.w[slot * 5], &ar.meta[slot]};
     f |= classify_store(L, y, dzeta, c, z, dpa, th, o);
     return f;
@@ -264,21 +295,100 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
     int flags = 0;
     WorkCount wc;
 
-    // images of the source centre: the warm start of the first samples
-    cxd cc[6], zc[5];
-    eq6_coeffs(L.s, L.m2, L.y0, cc);
-    initial_roots(L.s, L.y0, zc);
+    // Images of a point inside the source: the warm start of the first samples.
+    // The point is offset from the centre by rho/2 because Eq. 6 degenerates
+    // (c5 = 0, a root at infinity) when the source point sits on a lens, and
+    // source centres exactly on a lens are a common input.  This solve only
+    // provides starting points (every sample is then iterated to full FP64
+    // accuracy in either mode), so it runs in FP32 from a cold start; it is
+    // the same on every lane of the warp.
+    const cxd yw = {L.y0.x + 0.5 * L.rho * 0.7648421872844885, L.y0.y + 0.5 * L.rho * 0.6442176872376911};
+    cxd zc[5];
+    unsigned cmask = 0x1fu;  // real images of the warm-start point
+    cxf cf1[5];              // f' at those images
+    float crJ[5];            // 1/J at those images
     {
+        cxd cc[6];
+        eq6_coeffs(L.s, L.m2, yw, cc);
+        float ca[6];
+        abs_coeffs(cc, ca);
+        const float cm = fmaxf(fmaxf(fmaxf(ca[0], ca[1]), fmaxf(ca[2], ca[3])), fmaxf(ca[4], ca[5]));
+        const double sc = 1.0 / (double)cm;
+        cxf cf[6];
+        float caf[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            cf[k] = to_f(sc * cc[k]);
+            caf[k] = ca[k] / cm;
+        }
+        // cold start on a circle enclosing the roots
+        const float r0 = 1.5f * (1.0f + (float)L.s + sqrtf((float)norm2(yw)));
+        // unit vectors at angles 2 pi k/5 + 0.4
+        const float ux[5] = {0.92106099f, -0.08573535f, -0.97404836f, -0.51625964f, 0.65498235f};
+        const float uy[5] = {0.38941834f, 0.99631795f, 0.22634001f, -0.85643213f, -0.75564417f};
+        cxf zf[5];
+#pragma unroll
+        for (int k = 0; k < 5; k++) zf[k] = {-0.5f * (float)L.s + r0 * ux[k], r0 * uy[k]};
         float dpa[5];
-        int c64 = 0, c32 = 0;
-        flags |= solve_quintic<0>(cc, zc, dpa, 200, c64, c32);
-        if (lane == 0) wc.sw64 += c64;
+        int it = 0;
+        for (; it < 100; it++)
+            if (aberth_sweep<float>(cf, caf, zf, dpa, 2e-6f, 6e-8f)) break;
+        if (lane == 0) wc.sw32 += it + 1;
+        bool fin = true;
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            zc[i] = to_d(zf[i]);
+            fin = fin && isfinite(zf[i].x) && isfinite(zf[i].y);
+        }
+        if (!fin) initial_roots(L.s, L.y0, zc);
+        // real images by the residual pair test (Sec. 2.4.1), and the
+        // first-order response dz = (dzeta - conj(f') conj(dzeta))/J of each
+        // to a move dzeta of the source point (from differentiating Eq. 1)
+        const cxf ywf = to_f(yw);
+        const float sf = (float)L.s, m1f = (float)L.m1, m2f = (float)L.m2;
+        float aR[5];
+        cxf R[5];
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            const cxf d1 = inv(cxf{zf[i].x + sf, zf[i].y}), d2 = inv(zf[i]);
+            R[i] = ywf - zf[i] + conj(m1f * d1 + m2f * d2);
+            aR[i] = norm2(R[i]);
+            cf1[i] = m1f * (d1 * d1) + m2f * (d2 * d2);
+            const float J = 1.0f - norm2(cf1[i]);
+            crJ[i] = 1.0f / (fabsf(J) < 1e-30f ? 1e-30f : J);
+        }
+        int r4 = 0, r5 = 0;
+        float a3 = 0.f, a4 = 0.f, a5 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            int r = 0;
+#pragma unroll
+            for (int j = 0; j < 5; j++)
+                if (j != i) r += (aR[j] < aR[i]) || (aR[j] == aR[i] && j < i);
+            if (r == 2) a3 = aR[i];
+            if (r == 3) { r4 = i; a4 = aR[i]; }
+            if (r == 4) { r5 = i; a5 = aR[i]; }
+        }
+        cxf R45 = {0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 5; i++)
+            if (i == r4 || i == r5) R45 = R45 + R[i];
+        if (norm2(R45) < 1e-4f * a5 && a4 > 100.0f * a3) cmask &= ~((1u << r4) | (1u << r5));
     }
+    const float wx = (float)(yw.x - L.y0.x), wy = (float)(yw.y - L.y0.y), rhof = (float)L.rho;
 #pragma unroll
     for (int t = 0; t < SPL; t++) {
         const int k = lane * SPL + t;
+        const double th = twopi * k / SPI;
         cxd z[5] = {zc[0], zc[1], zc[2], zc[3], zc[4]};
-        flags |= limb_sample<PREC>(L, twopi * k / SPI, z, ar, k, wc);
+        float sn, cs;
+        sincosf((float)th, &sn, &cs);
+        const cxf dzeta = {rhof * cs - wx, rhof * sn - wy};
+        cxf dz[5];
+#pragma unroll
+        for (int i = 0; i < 5; i++) dz[i] = crJ[i] * (dzeta - conj(cf1[i]) * conj(dzeta));
+        predict_roots(z, dz, cmask);
+        flags |= limb_sample<PREC>(L, th, z, ar, k, wc);
         ar.ordA[k] = (uint16_t)k;
     }
     __syncwarp();
@@ -306,7 +416,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
         if (nslot + SPI > cap) { flags |= PS_CAP; break; }
 
         // cumulative error in theta order, each edge less its share of the tolerance
-        const double thr = tol * fabs(A) / N;
+        const double thr = tol * fabs(A) * rcp((double)N);
         const int chunk = (N + 31) >> 5;
         const int p0 = min(lane * chunk, N), p1 = min(p0 + chunk, N);
         double run = 0.0;
@@ -340,7 +450,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
             }
             const int sa = ordA[lo];
             const double wp = fmax(ar.eE[sa] - thr, 0.0);
-            double frac = (wp > 0.0) ? (target - (ar.cum[lo] - wp)) / wp : 0.5;
+            double frac = (wp > 0.0) ? (target - (ar.cum[lo] - wp)) * rcp(wp) : 0.5;
             frac = fmin(fmax(frac, 0.0), 1.0);
             const double ta = ar.theta[sa];
             const double tb = (lo + 1 < N) ? ar.theta[ordA[lo + 1]] : twopi;
@@ -390,8 +500,14 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
             if (tk[t]) {
                 const int sa = ordA[tp[t]];
                 cxd z[5];
+                cxf dz[5];
+                const float dth = (float)(tn[t] - ar.theta[sa]);
 #pragma unroll
-                for (int i = 0; i < 5; i++) z[i] = ar.roots[sa * 5 + i];
+                for (int i = 0; i < 5; i++) {
+                    z[i] = ar.roots[sa * 5 + i];
+                    dz[i] = dth * ar.zp[sa * 5 + i];
+                }
+                predict_roots(z, dz, real_mask(ar.meta[sa]));
                 flags |= limb_sample<PREC>(L, tn[t], z, ar, nslot + rk[t], wc);
             }
         // merge into theta order
@@ -437,6 +553,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
     r.work.sw64 = __reduce_add_sync(FULL, wc.sw64);
     r.work.sw32 = __reduce_add_sync(FULL, wc.sw32);
     r.work.edges = __reduce_add_sync(FULL, wc.edges);
+    r.work.nw64 = __reduce_add_sync(FULL, wc.nw64);
     r.area = A;
     r.err = E;
     r.nsamp = N;

@@ -1,9 +1,9 @@
 // cx.cuh -- minimal complex arithmetic for the device code (FP64 and FP32).
 //
-// Plain structs so that everything stays in registers; reciprocals use the
-// correctly rounded CUDA intrinsics.  The FP32 division rescales its divisor
-// first because polynomial values near a root of a low-mass-ratio lens can be
-// small enough for |b|^2 to underflow in single precision.
+// Plain structs so that everything stays in registers.  The FP32 division
+// rescales its divisor first because polynomial values near a root of a
+// low-mass-ratio lens can be small enough for |b|^2 to underflow in single
+// precision.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -39,8 +39,26 @@ __device__ __forceinline__ T wedge(cx<T> a, cx<T> b) { return a.x * b.y - a.y * 
 template <typename T>
 __device__ __forceinline__ T dot(cx<T> a, cx<T> b) { return a.x * b.x + a.y * b.y; }
 
-__device__ __forceinline__ double rcp(double v) { return __drcp_rn(v); }
-__device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+// FP64 reciprocal: the hardware approximation (rcp.approx.ftz.f64, about 20
+// correct bits) refined by two Newton-Raphson steps y <- y + y (1 - v y), each
+// of which doubles the number of correct bits.  Five FP64-pipe instructions
+// instead of an IEEE-rounded division; the last bit may differ from 1/v.
+// Inputs are kept in the normal range by the callers (|v| >= 1e-300).
+__device__ __forceinline__ double rcp(double v) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(v));
+    double e = fma(-v, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-v, y, 1.0);
+    return fma(y, e, y);
+}
+// FP32 reciprocal: the hardware approximation (rcp.approx.ftz.f32, ~1 ulp),
+// enough for the FP32 root iteration.
+__device__ __forceinline__ float rcp(float v) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+    return y;
+}
 
 __device__ __forceinline__ cxd inv(cxd a) {
     double r = rcp(fmax(norm2(a), 1e-300));

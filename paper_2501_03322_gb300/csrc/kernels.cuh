@@ -46,7 +46,8 @@ struct KParams {
     size_t slot_bytes;
     int cap;
     double tol;
-    unsigned long long *counter;  // [0]: next work item; [1..4]: samples, FP64 sweeps, FP32 sweeps, edges
+    unsigned long long *counter;  // [0]: next work item; [1..5]: samples, FP64 sweeps, FP32 sweeps, edges,
+                                  // FP64 Newton passes
 };
 
 struct PosIn {
@@ -58,7 +59,7 @@ __device__ __forceinline__ bool pos_ok(double v) { return isfinite(v); }
 // Straight-line trajectory (convention of twinkle.h).
 __device__ __forceinline__ void trajectory(double u0, double alpha, double t0, double tE, double t, double &y1,
                                            double &y2) {
-    const double tau = (t - t0) / tE;
+    const double tau = (t - t0) * rcp(tE);
     double sa, ca;
     sincos(alpha, &sa, &ca);
     y1 = tau * ca - u0 * sa;
@@ -106,16 +107,22 @@ __global__ void __launch_bounds__(TPB) contour_kernel(KParams kp) {
         double mu = __longlong_as_double(0x7ff8000000000000ll), err = mu;
         int nsamp = 0, status = PS_NONFINITE;
         if (valid) {
+            // Swapping the masses (q -> 1/q) reflects the lens through the centre
+            // of mass (Eq. 2), so mu(s, q, y1, y2) = mu(s, 1/q, -y1, y2).  Using it
+            // for q > 1 keeps the lighter body in the role of the low-mass lens of
+            // the refactored coefficients (Eq. 6).
+            double q = P.q, y1 = P.y1;
+            if (q > 1.0) { q = 1.0 / q; y1 = -y1; }
             LensK L;
             L.s = P.s;
-            L.m1 = 1.0 / (1.0 + P.q);
-            L.m2 = P.q / (1.0 + P.q);
+            L.m1 = rcp(1.0 + q);
+            L.m2 = q * L.m1;
             L.rho = P.rho;
-            L.y0 = {P.y1 - P.s / (1.0 + P.q), P.y2};  // centre-of-mass -> secondary frame
+            L.y0 = {y1 - P.s * L.m1, P.y2};  // centre-of-mass -> secondary frame
             const PosResult r = integrate_position<PREC, SPL>(L, kp.tol, kp.cap, ar, stage[wib]);
-            const double area_src = 3.141592653589793238 * P.rho * P.rho;
-            mu = r.area / area_src;
-            err = r.err / area_src;
+            const double inv_src = rcp(3.141592653589793238 * P.rho * P.rho);
+            mu = r.area * inv_src;
+            err = r.err * inv_src;
             nsamp = r.nsamp;
             status = r.status;
             if (lane == 0) {
@@ -123,6 +130,7 @@ __global__ void __launch_bounds__(TPB) contour_kernel(KParams kp) {
                 atomicAdd(kp.counter + 2, (unsigned long long)r.work.sw64);
                 atomicAdd(kp.counter + 3, (unsigned long long)r.work.sw32);
                 atomicAdd(kp.counter + 4, (unsigned long long)r.work.edges);
+                atomicAdd(kp.counter + 5, (unsigned long long)r.work.nw64);
             }
             if (!isfinite(mu)) { status |= PS_NONFINITE; mu = __longlong_as_double(0x7ff8000000000000ll); }
         }
@@ -149,6 +157,8 @@ __global__ void __launch_bounds__(TPB) contour_kernel(KParams kp) {
 #define TW_DECLARE_LAUNCHER(PREC, SPL)                                                           \
     cudaError_t launch_contour_##PREC##_##SPL(unsigned blocks, cudaStream_t st, const KParams &kp); \
     cudaError_t occupancy_contour_##PREC##_##SPL(int *occ);
+
+cudaError_t launch_rcp_selftest(unsigned long long *max_err_bits, int n, cudaStream_t st);
 
 TW_DECLARE_LAUNCHER(0, 1)
 TW_DECLARE_LAUNCHER(0, 2)

@@ -2,24 +2,30 @@
 //
 // Frame: origin on the secondary (the frame of Eq. 6): the primary (mass m1)
 // sits at -s, the secondary (mass m2) at 0; y = zeta - z2 and eta = z - z2,
-// z2 = s/(1+q) being the secondary's centre-of-mass coordinate (Eq. 2).
+// z2 = s/(1+q) being the secondary's centre-of-mass coordinate (Eq. 2).  The
+// caller arranges q <= 1 (mass-swap symmetry), so that the refactored
+// coefficients of Eq. 6 always treat the lighter body as the low-mass lens.
 //
 // Steps, each following the paper:
 //   coefficients   Eq. 6 (cancellation-free form), FP64
-//   roots          Aberth-Ehrlich simultaneous iteration, warm-started from a
+//   roots          Aberth-Ehrlich simultaneous iteration warm-started from a
 //                  neighbouring sample's roots.  FP64 mode iterates in FP64;
 //                  mixed mode iterates in FP32 and then takes one FP64 Newton
-//                  step per root (falling back to FP64 iteration when the
-//                  quadratic-convergence bound is not met).  The paper uses
-//                  the Skowron-Gould Newton/Laguerre solver (Sec. 2.2); any
-//                  solver returning the five roots computes the same thing.
+//                  step per root on the undeflated quintic (two where the
+//                  quadratic error bound of the first is not yet at the FP64
+//                  target), falling back to FP64 iteration when a step is not
+//                  well inside the root's basin.  The
+//                  paper uses the Skowron-Gould Newton/Laguerre solver
+//                  (Sec. 2.2); any solver returning the five roots computes
+//                  the same thing.
 //   ghost test     residual R_i of Eq. 12 in FP64; ghosts are the pair whose
 //                  residuals are equal and opposite (Sec. 2.4.1) and well above
 //                  the round-off level of those roots
-//   parity         sign of J (Eq. 7); a sample is accepted when it has 3 or 5
-//                  real images with parity sum -1 (Sec. 2.3)
+//   parity         sign of J (Eq. 7) in FP64; a sample is accepted when it has
+//                  3 or 5 real images with parity sum -1 (Sec. 2.3)
 //   derivatives    dz/dtheta = (zeta' - conj(f') conj(zeta'))/J and
-//                  z' ^ z'' = (rho^2 + Im(z'^2 zeta' f''))/J  (Eq. 10)
+//                  z' ^ z'' = (rho^2 + Im(z'^2 zeta' f''))/J  (Eq. 10), in FP32:
+//                  they only enter the parabolic corrections and error terms
 #pragma once
 #include <stdint.h>
 
@@ -31,7 +37,7 @@ namespace tw {
 enum : int { SF_IMAGECOUNT = 2, SF_SOLVER = 8 };
 
 struct LensK {
-    double s, m1, m2; // separation and normalised masses (Eq. 2)
+    double s, m1, m2; // separation and normalised masses (Eq. 2), m2 <= m1
     double rho;       // source radius
     cxd y0;           // source centre in the secondary's frame
 };
@@ -78,45 +84,85 @@ __device__ __forceinline__ void eq6_coeffs(double s, double m2, cxd y, cxd c[6])
     c[0] = (m2s * m2s) * y;
 }
 
-// One Gauss-Seidel sweep of the Aberth-Ehrlich iteration on the quintic c.
-// dpa[i] receives |p'(z_i)|.  Returns true when every correction is below
-// max(rtol |z_i|, 8 eps B_i/|p'(z_i)|), B_i being the Horner round-off bound
-// sum_k |c_k| |z_i|^k (the second term is the attainable accuracy of a
-// near-multiple root).
+__device__ __forceinline__ void abs_coeffs(const cxd c[6], float ca[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) ca[k] = sqrtf((float)norm2(c[k]));
+}
+
+// Horner round-off bound sum_k |c_k| |z|^k (the attainable residual |p(z)|).
+__device__ __forceinline__ float horner_bound(const float ca[6], float az) {
+    float B = ca[5];
+#pragma unroll
+    for (int k = 4; k >= 0; k--) B = B * az + ca[k];
+    return B;
+}
+
+// p(z) and p'(z) by Horner's rule.
+template <typename T>
+__device__ __forceinline__ void horner(const cx<T> c[6], cx<T> z, cx<T> &p, cx<T> &d) {
+    p = c[5];
+    d = {T(0), T(0)};
+#pragma unroll
+    for (int k = 4; k >= 0; k--) {
+        d = d * z + p;
+        p = p * z + c[k];
+    }
+}
+
+// One Jacobi sweep of the Aberth-Ehrlich iteration on the quintic c:
+// z_i <- z_i - w_i, w_i = p/(p' - p S_i), S_i = sum_{j != i} 1/(z_i - z_j), the
+// ten pair reciprocals being shared between the two roots of each pair.
+// dpa[i] receives |p'(z_i)|.  Returns true when every root is converged: its
+// correction, or the error left after it, is below
+// thr_i = max(rtol |z_i|, 8 eps B_i/|p'(z_i)|) (B_i the Horner round-off
+// bound; the second term is the attainable accuracy of a near-multiple root).
+// The iteration converges cubically, the error after a step being about
+// |w_i|^2 max_j|w_j| sum_j 1/|z_i - z_j|^2, so a sweep whose corrections are
+// already small needs no confirming sweep.
 template <typename T>
 __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6], cx<T> z[5], float dpa[5],
                                              float rtol, float eps) {
+    cx<T> S[5];
+    float K2[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) { S[i] = {T(0), T(0)}; K2[i] = 0.f; }
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+#pragma unroll
+        for (int j = i + 1; j < 5; j++) {
+            const cx<T> r = inv(z[i] - z[j]);
+            S[i] = S[i] + r;
+            S[j] = S[j] - r;
+            const float rr = (float)norm2(r);
+            K2[i] += rr;
+            K2[j] += rr;
+        }
+    cx<T> w[5];
+    float wa2[5], thr[5], wmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        cx<T> p, d;
+        horner(c, z[i], p, d);
+        w[i] = cdiv(p, d - p * S[i]);
+        const float az = sqrtf((float)norm2(z[i]));
+        const float dabs = sqrtf((float)norm2(d));
+        dpa[i] = dabs;
+        thr[i] = fmaxf(rtol * az, 8.0f * eps * horner_bound(ca, az) / fmaxf(dabs, 1e-37f));
+        wa2[i] = (float)norm2(w[i]);
+        wmax = fmaxf(wmax, wa2[i]);
+    }
+    wmax = sqrtf(wmax);
     bool conv = true;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
-        cx<T> p = c[5], d = {T(0), T(0)};
-        const float az = sqrtf((float)norm2(z[i]));
-        float B = ca[5];
-#pragma unroll
-        for (int k = 4; k >= 0; k--) {
-            d = d * z[i] + p;
-            p = p * z[i] + c[k];
-            B = B * az + ca[k];
-        }
-        const cx<T> ratio = cdiv(p, d);
-        cx<T> S = {T(0), T(0)};
-#pragma unroll
-        for (int j = 0; j < 5; j++)
-            if (j != i) S = S + inv(z[i] - z[j]);
-        const cx<T> rs = ratio * S;
-        const cx<T> w = cdiv(ratio, cx<T>{T(1) - rs.x, -rs.y});
-        z[i] = z[i] - w;
-        const float dabs = sqrtf((float)norm2(d));
-        dpa[i] = dabs;
-        const float wa = sqrtf((float)norm2(w));
-        const float thr = fmaxf(rtol * az, 8.0f * eps * B / fmaxf(dabs, 1e-37f));
-        conv = conv && (wa <= thr);
+        z[i] = z[i] - w[i];
+        const float after = wa2[i] * wmax * K2[i];
+        conv = conv && (wa2[i] <= thr[i] * thr[i] || after <= 0.25f * thr[i]);
     }
     return conv;
 }
 
-// Aberth starting points on a circle enclosing the roots (used once per
-// position, for the source centre).
+// Aberth starting points on a circle enclosing the roots (cold start).
 __device__ __forceinline__ void initial_roots(double s, cxd y0, cxd z[5]) {
     const double r = 1.5 * (1.0 + s + sqrt(norm2(y0)));
 #pragma unroll
@@ -127,28 +173,31 @@ __device__ __forceinline__ void initial_roots(double s, cxd y0, cxd z[5]) {
     }
 }
 
-__device__ __forceinline__ void abs_coeffs(const cxd c[6], float ca[6]) {
+__device__ __forceinline__ bool roots_finite(const cxd z[5]) {
+    bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 6; k++) ca[k] = (float)sqrt(norm2(c[k]));
+    for (int i = 0; i < 5; i++) ok = ok && isfinite(z[i].x) && isfinite(z[i].y);
+    return ok;
 }
 
-// Roots of the quintic c starting from z.  PREC 0: FP64 iteration; PREC 1:
-// FP32 iteration + FP64 Newton step per root, with FP64 iteration as the
-// fallback.  Returns SF_SOLVER when the iteration limit was reached.
+// Roots of the quintic c starting from z (see the header comment).  sw64 and
+// sw32 count FP64 and FP32 Aberth sweeps, nw64 FP64 Newton passes over the
+// five roots.  Returns SF_SOLVER when the iteration limit was reached.
 template <int PREC>
-__device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa[5], int maxit, int &sw64, int &sw32) {
+__device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa[5], int maxit, int &sw64, int &sw32,
+                                             int &nw64) {
     float ca[6];
     abs_coeffs(c, ca);
     if (PREC == 1) {
         // scale to unit largest coefficient so FP32 neither under- nor overflows
-        float cm = fmaxf(fmaxf(fmaxf(ca[0], ca[1]), fmaxf(ca[2], ca[3])), fmaxf(ca[4], ca[5]));
+        const float cm = fmaxf(fmaxf(fmaxf(ca[0], ca[1]), fmaxf(ca[2], ca[3])), fmaxf(ca[4], ca[5]));
         const double sc = 1.0 / (double)cm;
         cxf cf[6];
         float caf[6];
 #pragma unroll
         for (int k = 0; k < 6; k++) {
             cf[k] = to_f(sc * c[k]);
-            caf[k] = (float)(sc * ca[k]);
+            caf[k] = ca[k] / cm;
         }
         cxf zf[5];
 #pragma unroll
@@ -158,32 +207,48 @@ __device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa
             conv = aberth_sweep<float>(cf, caf, zf, dpa, 2e-6f, 6e-8f);
             sw32++;
         }
-        // one FP64 Newton step per root; accepted when |step|^2 * sum_j 1/|z_i - z_j|
-        // (the quadratic error bound) is below the FP64 target
-        bool ok = true;
+        // FP64 Newton steps per root on the undeflated quintic: the error left
+        // after a step of size st is about |st|^2 sum_j 1/|z_i - z_j|; one step
+        // from FP32 accuracy usually reaches the FP64 target, a second is taken
+        // where it does not.  Every first step must also be well inside the
+        // root's basin (small against the distance to the nearest other root).
+        bool ok = true, need2 = false;
+        float K[5], lim[5];
 #pragma unroll
         for (int i = 0; i < 5; i++) {
-            cxd zi = to_d(zf[i]);
-            cxd p = c[5], d = {0.0, 0.0};
-            const float az = sqrtf(norm2(zf[i]));
-            float B = ca[5];
-#pragma unroll
-            for (int k = 4; k >= 0; k--) {
-                d = d * zi + p;
-                p = p * zi + c[k];
-                B = B * az + ca[k];
-            }
-            const cxd step = cdiv(p, d);
-            z[i] = zi - step;
-            float K = 0.f;
+            float sep2 = 3.0e38f, k = 0.f;
 #pragma unroll
             for (int j = 0; j < 5; j++)
-                if (j != i) K += rsqrtf(fmaxf(norm2(zf[i] - zf[j]), 1e-37f));
-            const float st2 = (float)norm2(step);
+                if (j != i) {
+                    const float d2 = fmaxf(norm2(zf[i] - zf[j]), 1e-37f);
+                    sep2 = fminf(sep2, d2);
+                    k += rsqrtf(d2);
+                }
+            K[i] = k;
+            cxd zi = to_d(zf[i]), p, d;
+            horner(c, zi, p, d);
+            const cxd st = cdiv(p, d);
+            z[i] = zi - st;
+            const float az = sqrtf(norm2(zf[i]));
             const float dabs = sqrtf((float)norm2(d));
             dpa[i] = dabs;
-            const float tgt = fmaxf(1e-14f * az, 8.0f * 1.1e-16f * B / fmaxf(dabs, 1e-37f));
-            ok = ok && (st2 * K <= tgt) && isfinite(st2);
+            lim[i] = fmaxf(1e-13f * az, 8.0f * 1.1e-16f * horner_bound(ca, az) / fmaxf(dabs, 1e-37f));
+            const float s1 = (float)norm2(st);
+            ok = ok && (s1 <= 2.5e-3f * sep2) && isfinite(s1);
+            need2 = need2 || (s1 * k > lim[i]);
+        }
+        nw64++;
+        if (ok && need2) {
+#pragma unroll
+            for (int i = 0; i < 5; i++) {
+                cxd p, d;
+                horner(c, z[i], p, d);
+                const cxd st = cdiv(p, d);
+                z[i] = z[i] - st;
+                const float s2 = (float)norm2(st);
+                ok = ok && (s2 * K[i] <= lim[i]) && isfinite(s2);
+            }
+            nw64++;
         }
         if (ok) return 0;
         // fallback: FP64 iteration from the FP32 roots
@@ -201,8 +266,8 @@ __device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa
 struct SampleRefs {
     double *theta;
     cxd *roots;   // [5] all roots (warm starts for neighbours)
-    cxd *zp;      // [5] dz/dtheta of each root (meaningful for real images)
-    double *w;    // [5] z' ^ z''
+    cxf *zp;      // [5] dz/dtheta of each root (meaningful for real images)
+    float *w;     // [5] z' ^ z''
     uint32_t *meta;
 };
 
@@ -215,11 +280,12 @@ __device__ __forceinline__ int meta_index(uint32_t m, int k) { return (int)((m >
 // Classify the roots z of the sample at limb point y (secondary frame), with
 // limb tangent dzeta = i rho e^{i theta}; compute derivatives; store.
 // Returns the sample's status bits.
-__device__ __forceinline__ int classify_store(const LensK& L, cxd y, cxd dzeta, const cxd c[6], const cxd z[5],
+__device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, const cxd c[6], const cxd z[5],
                                               const float dpa[5], double theta, SampleRefs out) {
-    cxd R[5], f1[5], f2[5];
-    double aR[5], J[5];
-    float noise[5];
+    cxd R[5];
+    float aR[5], noise[5], Jf[5];
+    bool Jpos[5];
+    cxf f1f[5], d1f[5], d2f[5];
     float ca[6];
     abs_coeffs(c, ca);
 #pragma unroll
@@ -228,16 +294,17 @@ __device__ __forceinline__ int classify_store(const LensK& L, cxd y, cxd dzeta, 
         const cxd d2 = inv(z[i]);                      // 1/eta      = -1/(z2 - z)
         const cxd g = L.m1 * d1 + L.m2 * d2;           // = -f(z)
         R[i] = y - z[i] + conj(g);                     // Eq. 12
-        aR[i] = norm2(R[i]);
+        aR[i] = (float)norm2(R[i]);
         const cxd d1s = d1 * d1, d2s = d2 * d2;
-        f1[i] = L.m1 * d1s + L.m2 * d2s;               // f'(z)
-        f2[i] = -2.0 * (L.m1 * (d1s * d1) + L.m2 * (d2s * d2)); // f''(z)
-        J[i] = 1.0 - norm2(f1[i]);                     // Eq. 7
+        const cxd f1 = L.m1 * d1s + L.m2 * d2s;        // f'(z)
+        const double J = 1.0 - norm2(f1);              // Eq. 7
+        Jpos[i] = J > 0.0;
+        Jf[i] = (float)J;
+        f1f[i] = to_f(f1);
+        d1f[i] = to_f(d1);
+        d2f[i] = to_f(d2);
         const float az = sqrtf((float)norm2(z[i]));
-        float B = ca[5];
-#pragma unroll
-        for (int k = 4; k >= 0; k--) B = B * az + ca[k];
-        noise[i] = 1.1e-16f * B * (1.0f + (float)(fabs(f1[i].x) + fabs(f1[i].y))) / fmaxf(dpa[i], 1e-37f);
+        noise[i] = 1.1e-16f * horner_bound(ca, az) * (1.0f + fabsf(f1f[i].x) + fabsf(f1f[i].y)) / fmaxf(dpa[i], 1e-37f);
     }
     int rank[5];
 #pragma unroll
@@ -249,8 +316,7 @@ __device__ __forceinline__ int classify_store(const LensK& L, cxd y, cxd dzeta, 
         rank[i] = r;
     }
     cxd R4 = {0, 0}, R5 = {0, 0};
-    double a3 = 0, a4 = 0, a5 = 0;
-    float n45 = 0.f;
+    float a3 = 0.f, a4 = 0.f, a5 = 0.f, n45 = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         if (rank[i] == 2) a3 = aR[i];
@@ -259,15 +325,15 @@ __device__ __forceinline__ int classify_store(const LensK& L, cxd y, cxd dzeta, 
     }
     // Sec. 2.4.1: a ghost pair has equal and opposite residuals far above the
     // round-off level of those roots
-    const bool ghost = (norm2(R4 + R5) < 1e-4 * a5) && (a4 > 1e4 * (double)n45 * (double)n45) && (a4 > 100.0 * a3);
+    const bool ghost = ((float)norm2(R4 + R5) < 1e-4f * a5) && (a4 > 1e4f * n45 * n45) && (a4 > 100.0f * a3);
     int count = ghost ? 3 : 5;
     int flags = 0;
     // Sec. 2.3: 3 real images with one positive, or 5 with two positive
     int npos3 = 0, npos5 = 0;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
-        npos3 += (rank[i] < 3 && J[i] > 0);
-        npos5 += (J[i] > 0);
+        npos3 += (rank[i] < 3 && Jpos[i]);
+        npos5 += Jpos[i];
     }
     const bool ok3 = (npos3 == 1), ok5 = (npos5 == 2);
     if (count == 3 && !ok3 && ok5) count = 5;
@@ -275,29 +341,32 @@ __device__ __forceinline__ int classify_store(const LensK& L, cxd y, cxd dzeta, 
     else if (!(count == 3 ? ok3 : ok5)) flags |= SF_IMAGECOUNT;
 
     // derivatives (Eq. 10, with conj(f') in dz/dtheta) and storage
-    const double rho2 = L.rho * L.rho;
+    const cxf dzf = to_f(dzeta);
+    const float rho2 = (float)(L.rho * L.rho);
+    const float m1f = (float)L.m1, m2f = (float)L.m2;
     uint32_t meta = (uint32_t)count;
     int kp = 0, kn = (count - 1) / 2;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
-        double Ji = J[i];
-        if (fabs(Ji) < 1e-300) Ji = copysign(1e-300, Ji);
-        const double rJ = rcp(Ji);
-        const cxd num = dzeta - conj(f1[i]) * conj(dzeta);
-        const cxd zp = rJ * num;
-        const cxd t = (zp * zp) * (dzeta * f2[i]);
-        const double wv = (rho2 + t.y) * rJ;
+        float Ji = Jf[i];
+        if (fabsf(Ji) < 1e-30f) Ji = Jpos[i] ? 1e-30f : -1e-30f;
+        const float rJ = 1.0f / Ji;
+        const cxf num = dzf - conj(f1f[i]) * conj(dzf);
+        const cxf zp = rJ * num;
+        const cxf d1c = d1f[i] * d1f[i] * d1f[i], d2c = d2f[i] * d2f[i] * d2f[i];
+        const cxf f2 = -2.0f * (m1f * d1c + m2f * d2c); // f''(z)
+        const cxf t = (zp * zp) * (dzf * f2);
         out.roots[i] = z[i];
         out.zp[i] = zp;
-        out.w[i] = wv;
+        out.w[i] = (rho2 + t.y) * rJ;
         if (rank[i] < count) {
-            if (J[i] > 0 && kp < (count - 1) / 2) { meta |= (uint32_t)i << (3 + 3 * kp); kp++; }
-            else if (J[i] <= 0 && kn < count) { meta |= (uint32_t)i << (3 + 3 * kn); kn++; }
+            if (Jpos[i] && kp < (count - 1) / 2) { meta |= (uint32_t)i << (3 + 3 * kp); kp++; }
+            else if (!Jpos[i] && kn < count) { meta |= (uint32_t)i << (3 + 3 * kn); kn++; }
             else flags |= SF_IMAGECOUNT;
         }
     }
     if (flags & SF_IMAGECOUNT) {
-        // fall back to the residual order alone so the sample still has `count` images
+        // keep `count` images in residual order so the sample can still be linked
         meta = (uint32_t)count | (1u << 31);
         int k = 0;
 #pragma unroll

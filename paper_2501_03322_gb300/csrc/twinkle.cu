@@ -116,7 +116,7 @@ static int launch(DevState &d, const WorkSrc &src, double tol, const tw_opts &o,
     if (rc) return rc;
     // serialise with the previous launch (the arena and counter are shared)
     if ((e = cudaStreamWaitEvent(st, d.last, 0)) != cudaSuccess) return cuda_fail(e);
-    if ((e = cudaMemsetAsync(d.counter, 0, 5 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(d.counter, 0, 6 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_fail(e);
     KParams kp;
     kp.src = src;
     kp.out = out;
@@ -322,17 +322,34 @@ const char *tw_status_str(int code) {
 
 int tw_version(void) { return 100; }
 
-int tw_last_launch_work(int64_t out[4]) {
+int tw_selftest(double *rcp_max_rel_err) {
+    if (!rcp_max_rel_err) return TW_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState *dp = nullptr;
+    int rc = dev_state(&dp);
+    if (rc) return rc;
+    unsigned long long *slot = dp->counter + 6;  // scratch word of the control block
+    cudaError_t e = cudaStreamWaitEvent(0, dp->last, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(slot, 0, 8, 0);
+    if (e == cudaSuccess) e = launch_rcp_selftest(slot, 1 << 20, 0);
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, slot, 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    memcpy(rcp_max_rel_err, &h, 8);
+    return TW_OK;
+}
+
+int tw_last_launch_work(int64_t out[5]) {
     if (!out) return TW_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
     DevState *dp = nullptr;
     int rc = dev_state(&dp);
     if (rc) return rc;
     cudaError_t e = cudaEventSynchronize(dp->last);
-    unsigned long long h[5];
+    unsigned long long h[6];
     if (e == cudaSuccess) e = cudaMemcpy(h, dp->counter, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e);
-    for (int i = 0; i < 4; i++) out[i] = (int64_t)h[i + 1];
+    for (int i = 0; i < 5; i++) out[i] = (int64_t)h[i + 1];
     return TW_OK;
 }
 

@@ -158,3 +158,9 @@ def test_mirror_and_mass_swap_symmetry_full_size():
     d = P.mag(c["s"], 1.0 / c["q"], c["rho"], dev(-y1), dev(y2)).cpu().numpy()
     assert rel_err(a, b).max() <= 2 * TOL
     assert rel_err(a, d).max() <= 2 * TOL
+
+
+def test_device_reciprocal_against_ieee_division():
+    """The kernels' FP64 reciprocal (hardware approximation + two Newton-Raphson
+    steps) stays within a few ulp of IEEE division over 1e-300..1e300."""
+    assert P.selftest_rcp() <= 4.5e-16
