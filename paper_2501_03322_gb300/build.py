@@ -20,6 +20,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtwinkle_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# extra nvcc flags for experiments (e.g. -DTW_MIN_CTAS_PER_SM=3)
+FLAGS += os.environ.get("TW_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:

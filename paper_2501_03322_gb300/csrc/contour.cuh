@@ -148,13 +148,15 @@ __device__ __forceinline__ constexpr int perm_at(int p, int i) {
           :          (i == 0 ? 2 : i == 1 ? 1 : 0));
 }
 
-// Link the NX images X of one parity class at the edge's start to the NY
-// images Y of the same class at its end (|NX - NY| <= 1) so that the total
-// distance is minimal (Sec. 2.3; ties go to the lowest permutation).  The one
-// image left over when NX != NY is returned in `left`.
+// Link the NX images of one parity class at the edge's start (positions X,
+// class slots x0..x0+NX-1) to the NY images of that class at its end (Y,
+// y0..), |NX - NY| <= 1, so that the total distance is minimal (Sec. 2.3;
+// ties go to the lowest permutation).  Appends each link as a 3-bit start
+// slot, a 3-bit end slot and a parity bit to `links`; returns the slot of the
+// image left over when NX != NY (else -1).
 template <int NX, int NY>
-__device__ __forceinline__ void link_class(const Img *X, const Img *Y, double sgn, float dth, double &dA, float &dE,
-                                           Img &left) {
+__device__ __forceinline__ int link_class(const cxd *X, const cxd *Y, int x0, int y0, unsigned neg, uint64_t &links,
+                                          int &nlinks) {
     constexpr int N = NX > NY ? NX : NY;
     constexpr int M = NX > NY ? NY : NX;
     constexpr int NP = N == 1 ? 1 : (N == 2 ? 2 : 6);
@@ -166,59 +168,79 @@ __device__ __forceinline__ void link_class(const Img *X, const Img *Y, double sg
 #pragma unroll
         for (int i = 0; i < M; i++) {
             const int j = perm_at<N>(p, i);
-            const cxf d = to_f((NX <= NY) ? (Y[j].z - X[i].z) : (Y[i].z - X[j].z));
+            const cxf d = to_f((NX <= NY) ? (Y[y0 + j] - X[x0 + i]) : (Y[y0 + i] - X[x0 + j]));
             cost += sqrtf(norm2(d));
         }
         if (cost < best_cost) { best_cost = cost; best = p; }
     }
+    int left = -1;
 #pragma unroll
     for (int p = 0; p < NP; p++) {
         if (p == best) {
 #pragma unroll
             for (int i = 0; i < M; i++) {
                 const int j = perm_at<N>(p, i);
-                if (NX <= NY) link_contrib(X[i], Y[j], sgn, dth, dA, dE);
-                else link_contrib(X[j], Y[i], sgn, dth, dA, dE);
+                const unsigned a = (unsigned)(NX <= NY ? x0 + i : x0 + j), b = (unsigned)(NX <= NY ? y0 + j : y0 + i);
+                links |= (uint64_t)(a | (b << 3) | (neg << 6)) << (7 * nlinks);
+                nlinks++;
             }
-            if (NX < NY) left = Y[perm_at<N>(p, N - 1)];
-            if (NX > NY) left = X[perm_at<N>(p, N - 1)];
+            if (NX < NY) left = y0 + perm_at<N>(p, N - 1);
+            if (NX > NY) left = x0 + perm_at<N>(p, N - 1);
         }
     }
+    return left;
 }
 
+// Linking of one edge given the image positions of its two samples (class
+// slots in parity order, positives first).  lp/ln: slots of the extra
+// positive/negative image when the count changes.
 template <int NA, int NB>
-__device__ __forceinline__ void edge_case(const Img *IA, const Img *IB, float dth, double &dA, float &dE) {
+__device__ __forceinline__ void edge_links(const cxd *ZA, const cxd *ZB, uint64_t &links, int &nlinks, int &lp, int &ln) {
     constexpr int PA = (NA - 1) / 2, PB = (NB - 1) / 2;
-    Img lp, ln;
-    link_class<PA, PB>(IA, IB, 1.0, dth, dA, dE, lp);
-    link_class<NA - PA, NB - PB>(IA + PA, IB + PB, -1.0, dth, dA, dE, ln);
-    if (NA < NB) pair_contrib(lp, ln, true, dth, dA, dE);
-    if (NA > NB) pair_contrib(lp, ln, false, dth, dA, dE);
+    lp = link_class<PA, PB>(ZA, ZB, 0, 0, 0u, links, nlinks);
+    ln = link_class<NA - PA, NB - PB>(ZA, ZB, PA, PB, 1u, links, nlinks);
+}
+
+__device__ __forceinline__ Img load_img(const Arena &ar, int slot, uint32_t meta, int k) {
+    const int i = slot * 5 + meta_index(meta, k);
+    Img m;
+    m.z = ar.roots[i];
+    m.zp = ar.zp[i];
+    m.w = ar.w[i];
+    return m;
 }
 
 // Area and error of the edge from sample slot sa to slot sb (angle step dth).
 static __device__ __noinline__ void compute_edge(const Arena &ar, int sa, int sb, double dth, double *outA, double *outE) {
     const uint32_t ma = ar.meta[sa], mb = ar.meta[sb];
     const int na = meta_count(ma), nb = meta_count(mb);
-    Img IA[5], IB[5];
+    cxd ZA[5], ZB[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-        if (k < na) {
-            const int i = sa * 5 + meta_index(ma, k);
-            IA[k].z = ar.roots[i]; IA[k].zp = ar.zp[i]; IA[k].w = ar.w[i];
-        }
-        if (k < nb) {
-            const int i = sb * 5 + meta_index(mb, k);
-            IB[k].z = ar.roots[i]; IB[k].zp = ar.zp[i]; IB[k].w = ar.w[i];
-        }
+        if (k < na) ZA[k] = ar.roots[sa * 5 + meta_index(ma, k)];
+        if (k < nb) ZB[k] = ar.roots[sb * 5 + meta_index(mb, k)];
     }
+    uint64_t links = 0;
+    int nlinks = 0, lp = -1, ln = -1;
+    if (na == 3 && nb == 3) edge_links<3, 3>(ZA, ZB, links, nlinks, lp, ln);
+    else if (na == 5 && nb == 5) edge_links<5, 5>(ZA, ZB, links, nlinks, lp, ln);
+    else if (na == 3) edge_links<3, 5>(ZA, ZB, links, nlinks, lp, ln);
+    else edge_links<5, 3>(ZA, ZB, links, nlinks, lp, ln);
     double dA = 0.0;
     float dE = 0.0f;
     const float dthf = (float)dth;
-    if (na == 3 && nb == 3) edge_case<3, 3>(IA, IB, dthf, dA, dE);
-    else if (na == 5 && nb == 5) edge_case<5, 5>(IA, IB, dthf, dA, dE);
-    else if (na == 3) edge_case<3, 5>(IA, IB, dthf, dA, dE);
-    else edge_case<5, 3>(IA, IB, dthf, dA, dE);
+    for (int k = 0; k < nlinks; k++) {
+        const unsigned l = (unsigned)(links >> (7 * k)) & 127u;
+        const Img a = load_img(ar, sa, ma, (int)(l & 7u)), b = load_img(ar, sb, mb, (int)((l >> 3) & 7u));
+        link_contrib(a, b, (l >> 6) ? -1.0 : 1.0, dthf, dA, dE);
+    }
+    if (na != nb) {
+        // the extra pair belongs to the five-image end of the edge
+        const bool creation = na < nb;
+        const int sl = creation ? sb : sa;
+        const uint32_t ml = creation ? mb : ma;
+        pair_contrib(load_img(ar, sl, ml, lp), load_img(ar, sl, ml, ln), creation, dthf, dA, dE);
+    }
     double dEd = (double)dE;
     // a sample that failed the image-count check: keep refining around it
     if ((ma | mb) >> 31) dEd += fabs(dA);
@@ -259,8 +281,8 @@ __device__ __forceinline__ unsigned real_mask(uint32_t meta) {
 }
 
 template <int PREC>
-__device__ __forceinline__ int limb_sample(const LensK &L, double th, cxd z[5], const Arena &ar, int slot,
-                                           WorkCount &wc) {
+static __device__ __noinline__ int limb_sample(const LensK &L, double th, cxd z[5], const Arena &ar, int slot,
+                                               WorkCount &wc) {
     double sn, cs;
     sincos(th, &sn, &cs);
     const cxd y = {L.y0.x + L.rho * cs, L.y0.y + L.rho * sn};

@@ -23,6 +23,9 @@ namespace tw {
 
 constexpr int TPB = 128;  // 4 warps per CTA
 constexpr int WPB = TPB / 32;
+#ifndef TW_MIN_CTAS_PER_SM
+#define TW_MIN_CTAS_PER_SM 2  // register budget: 65536 / (128 x 2) = 256 per thread
+#endif
 
 // Where the positions of a launch come from.
 struct WorkSrc {
@@ -92,7 +95,7 @@ __device__ __forceinline__ bool fetch_position(const WorkSrc &w, int64_t idx, Po
 }
 
 template <int PREC, int SPL>
-__global__ void __launch_bounds__(TPB) contour_kernel(KParams kp) {
+__global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParams kp) {
     __shared__ WarpStage stage[WPB];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * WPB + wib;
