@@ -54,6 +54,8 @@ enum {
     TW_ECUDA = -2,    /* a CUDA runtime call failed (no device, launch error) */
     TW_ENOMEM = -3,   /* device working memory could not be allocated */
     TW_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    TW_ETOOBIG = -5,  /* tw_mag_noalloc: the request needs more scratch than its
+                         static array holds (max_samples > 512) */
     TW_WCAP = 1       /* synchronous call: >= 1 position reached the sample cap;
                          its output holds the best estimate */
 };
@@ -118,6 +120,24 @@ int tw_lightcurve_ex(double s, double q, double rho, double u0, double alpha, do
  * optional per-position outputs).  Total positions = offsets[ncurve]. */
 int tw_lightcurve_batch(const double *params, const int64_t *offsets, const double *times,
                         int64_t ncurve, double rel_tol, double *out, const tw_opts *opts);
+
+/* tw_mag without any device memory allocation, for callers that cannot
+ * allocate: code being captured into a CUDA graph, applications whose device
+ * memory belongs to their own pool or arena, and real-time loops in which an
+ * allocation could stall or fail.  (The paper has no counterpart: it
+ * describes no API.)  It computes what tw_mag_ex computes, with the given
+ * precision (TW_PREC_*) and sample cap max_samples (64..512), on `stream`.
+ * y1, y2 and out must be device pointers of the current device; the call is
+ * asynchronous.  The library's scratch for this entry point is one static
+ * device array of about 53 MiB (608 warp arenas of 512 limb samples plus a
+ * work counter), which every GPU that loads the library keeps until the
+ * process exits.  max_samples > 512 returns TW_ETOOBIG and writes nothing.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call reuses the same array
+ * (it clears the work counter itself), so calls that overlap on the GPU race
+ * and corrupt each other's results: serialise them. */
+int tw_mag_noalloc(double s, double q, double rho, const double *y1, const double *y2, int64_t n,
+                   double rel_tol, double *out, int precision, int max_samples, void *stream);
 
 /* Text of a return code (TW_OK, TW_E*, TW_WCAP). */
 const char *tw_status_str(int code);

@@ -25,7 +25,7 @@ import numpy as np
 
 from . import build as _build
 
-TW_OK, TW_EINVAL, TW_ECUDA, TW_ENOMEM, TW_ETIMEOUT, TW_WCAP = 0, -1, -2, -3, -4, 1
+TW_OK, TW_EINVAL, TW_ECUDA, TW_ENOMEM, TW_ETIMEOUT, TW_ETOOBIG, TW_WCAP = 0, -1, -2, -3, -4, -5, 1
 POS_CAP, POS_IMAGECOUNT, POS_NONFINITE, POS_SOLVER = 1, 2, 4, 8
 PREC_FP64, PREC_MIXED = 0, 1
 
@@ -86,6 +86,8 @@ def lib():
             L.tw_last_launch_work.restype = I
             L.tw_selftest.argtypes = [P]
             L.tw_selftest.restype = I
+            L.tw_mag_noalloc.argtypes = [d, d, d, P, P, i64, d, P, I, I, P]
+            L.tw_mag_noalloc.restype = I
             _lib = L
     return _lib
 
@@ -187,6 +189,22 @@ def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=6
     o = make_opts(precision, samples_per_iter, max_samples, _stream_of(y1, stream), err, nsamp, status)
     _check(lib().tw_mag_ex(s, q, rho, _ptr(y1), _ptr(y2), n, rel_tol, _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
+
+
+def mag_noalloc(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, max_samples=512, out=None, stream=None):
+    """tw_mag_noalloc: like mag() but the library allocates no device memory
+    (its scratch is a static device array).  y1, y2 and out must be CUDA
+    tensors; the call is asynchronous on the given or current stream."""
+    if not (_is_torch_cuda(y1) and _is_torch_cuda(y2)):
+        raise TypeError("mag_noalloc needs CUDA tensors")
+    y1, y2 = y1.contiguous(), y2.contiguous()
+    n = int(y1.shape[0])
+    if out is None:
+        out = _alloc_like(y1, n, np.float64, "float64")
+    st = _stream_of(y1, stream)
+    _check(lib().tw_mag_noalloc(s, q, rho, _ptr(y1), _ptr(y2), n, rel_tol, _ptr(out), int(precision),
+                                int(max_samples), st))
+    return out
 
 
 def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,

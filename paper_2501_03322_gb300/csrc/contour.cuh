@@ -51,11 +51,11 @@ struct Arena {
     double *cum;
 };
 
-__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+__host__ __device__ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Bytes of one warp slot for a sample cap `cap`.
-__host__ __device__ inline size_t arena_slot_bytes(int cap) {
-    size_t c = (size_t)cap;
+__host__ __device__ constexpr size_t arena_slot_bytes(int cap) {
+    const size_t c = (size_t)cap;
     return align256(c * 8) + align256(c * 5 * 16) + align256(c * 5 * 8) + align256(c * 5 * 4) + align256(c * 4) +
            align256(c * 8) * 2 + align256(c * 2) * 2 + align256(c * 8);
 }

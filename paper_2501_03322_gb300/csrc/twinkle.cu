@@ -314,6 +314,7 @@ const char *tw_status_str(int code) {
         case TW_ECUDA: return "CUDA runtime error";
         case TW_ENOMEM: return "out of device memory";
         case TW_ETIMEOUT: return "device-side wait timed out";
+        case TW_ETOOBIG: return "request exceeds the static scratch of tw_mag_noalloc (max_samples > 512)";
         case TW_WCAP: return "sample cap reached for at least one position";
         default: break;
     }
