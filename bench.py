@@ -87,12 +87,16 @@ def config_of(wl, mode, n_gpus):
     return cfg
 
 
+KERNEL_SOURCES = ("cx.cuh", "lens.cuh", "contour.cuh", "kernels.cuh", "k_fp64_spl1.cu", "k_fp64_spl2.cu",
+                  "k_fp64_spl4.cu", "k_mixed_spl1.cu", "k_mixed_spl2.cu", "k_mixed_spl4.cu")
+
+
 def sources_sha():
+    """Hash of the contour kernel's device sources (host runtime excluded)."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2501_03322_gb300", "csrc")
-    for fn in sorted(os.listdir(cs)):
-        if fn.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(cs, fn), "rb").read())
+    for fn in KERNEL_SOURCES:
+        h.update(open(os.path.join(cs, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -228,6 +232,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=128, help="positions in the CPU oracle baseline sample")
     ap.add_argument("--ref-sample", type=int, default=24, help="positions per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="let the library choose the launch shape")
+    ap.add_argument("--graph", action="store_true", help="replay each launch from a CUDA graph")
     ap.add_argument("--limit", type=int, default=0,
                     help="use a seeded sub-sample of this many positions (small profiling captures)")
     args = ap.parse_args()
@@ -241,6 +247,8 @@ def main():
         idx = W.sample_indices(wl["n"], args.limit, seed=4242)
         wl.update(y1=wl["y1"][idx], y2=wl["y2"][idx], n=idx.size, name=wl["name"] + "_sub%d" % idx.size)
     cfg = config_of(wl, args.mode, args.gpus)
+    cfg["autotune"] = bool(args.autotune)
+    cfg["graph"] = bool(args.graph)
     if args.impl == "reference":
         run_reference(args, wl, cfg, metric, unit)
         return
@@ -261,7 +269,10 @@ def main():
     import paper_2501_03322_gb300 as P
 
     prec = P.PREC_FP64 if args.mode == "fp64" else P.PREC_MIXED
+    if args.graph:  # graph capture needs a stream other than the legacy default one
+        torch.cuda.set_stream(torch.cuda.Stream(dev))
     stream = torch.cuda.current_stream(dev)
+    kw = dict(precision=prec, autotune=args.autotune, use_graph=args.graph)
 
     def D(a, dt=torch.float64):
         return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
@@ -271,20 +282,20 @@ def main():
         outd = torch.empty_like(y1d)
 
         def step():
-            P.mag(wl["s"], wl["q"], wl["rho"], y1d, y2d, rel_tol=wl["rel_tol"], precision=prec, out=outd)
+            P.mag(wl["s"], wl["q"], wl["rho"], y1d, y2d, rel_tol=wl["rel_tol"], out=outd, **kw)
     elif wl["kind"] == "lc":
         td = D(wl["times"])
         outd = torch.empty_like(td)
 
         def step():
             P.lightcurve(wl["s"], wl["q"], wl["rho"], wl["u0"], wl["alpha"], wl["t0"], wl["tE"], td,
-                         rel_tol=wl["rel_tol"], precision=prec, out=outd)
+                         rel_tol=wl["rel_tol"], out=outd, **kw)
     else:
         pd, od, td = D(wl["params"]), D(wl["offsets"], torch.int64), D(wl["times"])
         outd = torch.empty_like(td)
 
         def step():
-            P.lightcurve_batch(pd, od, td, rel_tol=wl["rel_tol"], precision=prec, out=outd)
+            P.lightcurve_batch(pd, od, td, rel_tol=wl["rel_tol"], out=outd, **kw)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
@@ -333,7 +344,7 @@ def main():
 
         def e2e_step():
             P.mag(wl["s"], wl["q"], wl["rho"], hy1.numpy(), hy2.numpy(), rel_tol=wl["rel_tol"], precision=prec,
-                  out=hout.numpy())
+                  autotune=args.autotune, out=hout.numpy())
     elif wl["kind"] == "lc":
         ht = torch.from_numpy(np.ascontiguousarray(wl["times"])).pin_memory()
         hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()
@@ -341,7 +352,7 @@ def main():
 
         def e2e_step():
             P.lightcurve(wl["s"], wl["q"], wl["rho"], wl["u0"], wl["alpha"], wl["t0"], wl["tE"], ht.numpy(),
-                         rel_tol=wl["rel_tol"], precision=prec, out=hout.numpy())
+                         rel_tol=wl["rel_tol"], precision=prec, autotune=args.autotune, out=hout.numpy())
     else:
         hp = torch.from_numpy(wl["params"]).pin_memory()
         ho = torch.from_numpy(wl["offsets"]).pin_memory()
@@ -352,7 +363,7 @@ def main():
 
         def e2e_step():
             P.lightcurve_batch(hp.numpy(), ho.numpy(), ht.numpy(), rel_tol=wl["rel_tol"], precision=prec,
-                               out=hout.numpy())
+                               autotune=args.autotune, out=hout.numpy())
     e2e_step()
     if dist:
         dist.barrier()

@@ -83,8 +83,15 @@ typedef struct tw_opts {
     int samples_per_iter; /* limb samples added per iteration and initial sample
                              count: 32, 64 (default, Sec. 3) or 128 */
     int max_samples;      /* sample cap per position, 64..16384 (default 4096, Sec. 3) */
-    int autotune;         /* 1: choose the launch shape by timing a calibration
-                             subsample, cached per (GPU, mode, tolerance) */
+    int autotune;         /* 1: choose the launch shape (samples per iteration,
+                             CTAs per SM, work items per grab) by timing a ~5%
+                             calibration sub-sample; cached per (GPU, precision,
+                             tolerance decade, workload kind) in memory and in
+                             $TW_AUTOTUNE_CACHE (default
+                             $HOME/.cache/twinkle_gb300_autotune.txt).  It
+                             overrides samples_per_iter. */
+    int use_graph;        /* 1: replay the launch from a CUDA graph captured on
+                             `stream` (needs a non-NULL stream; device pointers) */
     void *stream;         /* cudaStream_t for device-pointer calls, or NULL */
     double *err_out;      /* optional [n]: error estimate of mu (absolute) */
     int32_t *nsamp_out;   /* optional [n]: limb samples used */

@@ -45,6 +45,7 @@ class TwOpts(ctypes.Structure):
         ("samples_per_iter", ctypes.c_int),
         ("max_samples", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("err_out", ctypes.c_void_p),
         ("nsamp_out", ctypes.c_void_p),
@@ -129,9 +130,11 @@ def _alloc_like(ref, n, dtype_np, dtype_torch_name):
 
 
 def make_opts(precision=PREC_FP64, samples_per_iter=64, max_samples=4096, stream=None, err=None, nsamp=None,
-              status=None) -> TwOpts:
+              status=None, autotune=False, use_graph=False) -> TwOpts:
     o = TwOpts()
     lib().tw_opts_default(ctypes.byref(o))
+    o.autotune = int(bool(autotune))
+    o.use_graph = int(bool(use_graph))
     o.precision = int(precision)
     o.samples_per_iter = int(samples_per_iter)
     o.max_samples = int(max_samples)
@@ -173,7 +176,7 @@ def selftest_rcp() -> float:
 
 
 def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64, max_samples=4096,
-        out=None, details=False, stream=None):
+        out=None, details=False, stream=None, autotune=False, use_graph=False):
     """Finite-source magnification of positions (y1[i], y2[i]) (tw_mag_ex).
 
     Returns ``out`` or, with details=True, (out, err, nsamp, status)."""
@@ -186,7 +189,8 @@ def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=6
         err = _alloc_like(y1, n, np.float64, "float64")
         nsamp = _alloc_like(y1, n, np.int32, "int32")
         status = _alloc_like(y1, n, np.int8, "int8")
-    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(y1, stream), err, nsamp, status)
+    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(y1, stream), err, nsamp, status, autotune,
+                  use_graph)
     _check(lib().tw_mag_ex(s, q, rho, _ptr(y1), _ptr(y2), n, rel_tol, _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
 
@@ -208,7 +212,7 @@ def mag_noalloc(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, max_sample
 
 
 def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,
-               max_samples=4096, out=None, details=False, stream=None):
+               max_samples=4096, out=None, details=False, stream=None, autotune=False, use_graph=False):
     """Magnification along a straight-line trajectory (tw_lightcurve_ex)."""
     times = _prep(times)
     n = int(times.shape[0])
@@ -219,13 +223,14 @@ def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC
         err = _alloc_like(times, n, np.float64, "float64")
         nsamp = _alloc_like(times, n, np.int32, "int32")
         status = _alloc_like(times, n, np.int8, "int8")
-    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status)
+    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status, autotune,
+                  use_graph)
     _check(lib().tw_lightcurve_ex(s, q, rho, u0, alpha, t0, tE, _ptr(times), n, rel_tol, _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
 
 
 def lightcurve_batch(params, offsets, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,
-                     max_samples=4096, out=None, details=False, stream=None):
+                     max_samples=4096, out=None, details=False, stream=None, autotune=False, use_graph=False):
     """Many light curves in one launch (tw_lightcurve_batch).
 
     params: [ncurve, 7] (s, q, rho, u0, alpha, t0, tE); offsets: [ncurve + 1] int64."""
@@ -245,7 +250,8 @@ def lightcurve_batch(params, offsets, times, rel_tol=1e-4, precision=PREC_FP64, 
         err = _alloc_like(times, total, np.float64, "float64")
         nsamp = _alloc_like(times, total, np.int32, "int32")
         status = _alloc_like(times, total, np.int8, "int8")
-    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status)
+    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status, autotune,
+                  use_graph)
     _check(lib().tw_lightcurve_batch(_ptr(params), _ptr(offsets), _ptr(times), ncurve, rel_tol, _ptr(out),
                                      ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out

@@ -98,11 +98,13 @@ extern "C" int tw_mag_noalloc(double s, double q, double rho, const double *y1, 
     kp.src.rho = rho;
     kp.src.y1 = y1;
     kp.src.y2 = y2;
+    kp.src.stride = 1;
     kp.out = out;
     kp.arena = base + NOALLOC_HEADER;
     kp.slot_bytes = NOALLOC_SLOT_BYTES;
     kp.cap = (max_samples + 63) & ~63;
     kp.tol = rel_tol;
+    kp.chunk = 1;
     kp.counter = (unsigned long long *)base;
     // the work counter must start at zero; the arenas need no clearing
     if (cudaMemsetAsync(base, 0, NOALLOC_HEADER, st) != cudaSuccess) { (void)cudaGetLastError(); return TW_ECUDA; }

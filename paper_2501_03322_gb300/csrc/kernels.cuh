@@ -38,6 +38,8 @@ struct WorkSrc {
     const double *params;                  // kind 2: [ncurve][7]
     const int64_t *offsets;                // kind 2: [ncurve + 1]
     int64_t ncurve;
+    int64_t stride;                        // work item i is input position i * stride (calibration
+                                           // sub-samples use stride > 1; outputs stay compact)
 };
 
 struct KParams {
@@ -49,6 +51,7 @@ struct KParams {
     size_t slot_bytes;
     int cap;
     double tol;
+    int chunk;                    // consecutive work items taken per atomic grab
     unsigned long long *counter;  // [0]: next work item; [1..5]: samples, FP64 sweeps, FP32 sweeps, edges,
                                   // FP64 Newton passes
 };
@@ -100,13 +103,18 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParam
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * WPB + wib;
     const Arena ar = arena_at(kp.arena, kp.slot_bytes, kp.cap, gw);
+    unsigned long long idx = 0, end = 0;
     for (;;) {
-        unsigned long long idx = 0;
-        if (lane == 0) idx = atomicAdd(kp.counter, 1ull);
-        idx = __shfl_sync(FULL, idx, 0);
-        if (idx >= (unsigned long long)kp.src.n) break;
+        if (idx >= end) {
+            unsigned long long first = 0;
+            if (lane == 0) first = atomicAdd(kp.counter, (unsigned long long)kp.chunk);
+            idx = __shfl_sync(FULL, first, 0);
+            end = idx + (unsigned long long)kp.chunk;
+            if (end > (unsigned long long)kp.src.n) end = (unsigned long long)kp.src.n;
+            if (idx >= end) break;
+        }
         PosIn P;
-        const bool valid = fetch_position(kp.src, (int64_t)idx, P);
+        const bool valid = fetch_position(kp.src, (int64_t)idx * kp.src.stride, P);
         double mu = __longlong_as_double(0x7ff8000000000000ll), err = mu;
         int nsamp = 0, status = PS_NONFINITE;
         if (valid) {
@@ -143,6 +151,7 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParam
             if (kp.nsamp) kp.nsamp[idx] = nsamp;
             if (kp.pstat) kp.pstat[idx] = (int8_t)status;
         }
+        idx++;
     }
 }
 

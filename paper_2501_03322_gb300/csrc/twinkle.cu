@@ -4,7 +4,13 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+#include <sys/stat.h>
+
+#include <map>
 #include <mutex>
+#include <string>
 
 #include "../../include/twinkle.h"
 #include "kernels.cuh"
@@ -37,6 +43,10 @@ struct DevState {
     char *stage = nullptr;          // device staging for host-pointer calls
     size_t stage_bytes = 0;
     cudaEvent_t last = nullptr;     // completion of the previous launch (serialises calls)
+    char *calib = nullptr;          // outputs of autotuning calibration runs
+    size_t calib_bytes = 0;
+    cudaGraphExec_t graph = nullptr;  // replayable {counter reset, persistent kernel}
+    char name[256] = {0};           // device name (autotune cache key)
 };
 
 static std::mutex g_mu;
@@ -57,6 +67,9 @@ static int dev_state(DevState **out) {
         if ((e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e);
         if ((e = cudaMalloc(&d.counter, 64)) != cudaSuccess) return cuda_fail(e);
         if ((e = cudaEventCreateWithFlags(&d.last, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e);
+        cudaDeviceProp prop;
+        if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return cuda_fail(e);
+        snprintf(d.name, sizeof(d.name), "%s", prop.name);
         d.init = true;
     }
     *out = &d;
@@ -95,18 +108,28 @@ static int check_opts(const tw_opts *o) {
     return TW_OK;
 }
 
+// Launch shape: samples per lane per iteration (limb samples per iteration =
+// 32 x spl), CTAs per SM (0: as many as fit), work items per atomic grab.
+struct LaunchCfg {
+    int spl, ctas, chunk;
+};
+
 // Launches the contour kernel over src.n positions.  Device pointers only.
-static int launch(DevState &d, const WorkSrc &src, double tol, const tw_opts &o, double *out, double *err,
-                  int32_t *nsamp, int8_t *pstat, cudaStream_t st) {
-    const int spl = o.samples_per_iter / 32;
-    const int cap = (o.max_samples + 63) & ~63;
+// With use_graph the counter reset and the kernel are replayed from a CUDA
+// graph (captured on the call's stream and updated in place on later calls)
+// instead of being launched one by one.
+static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_samples, LaunchCfg cfg, bool use_graph,
+                  double *out, double *err, int32_t *nsamp, int8_t *pstat, cudaStream_t st) {
+    const int cap = (max_samples + 63) & ~63;
+    if (src.stride < 1) src.stride = 1;
     launch_fn lf;
     occ_fn of;
-    pick_kernel(o.precision, spl, &lf, &of);
+    pick_kernel(prec, cfg.spl, &lf, &of);
     int occ = 0;
     cudaError_t e = of(&occ);
     if (e != cudaSuccess) return cuda_fail(e);
     if (occ < 1) occ = 1;
+    if (cfg.ctas > 0 && cfg.ctas < occ) occ = cfg.ctas;
     int64_t blocks = (int64_t)d.nsm * occ;
     const int64_t need_blocks = (src.n + WPB - 1) / WPB;
     if (blocks > need_blocks) blocks = need_blocks;
@@ -116,7 +139,6 @@ static int launch(DevState &d, const WorkSrc &src, double tol, const tw_opts &o,
     if (rc) return rc;
     // serialise with the previous launch (the arena and counter are shared)
     if ((e = cudaStreamWaitEvent(st, d.last, 0)) != cudaSuccess) return cuda_fail(e);
-    if ((e = cudaMemsetAsync(d.counter, 0, 6 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_fail(e);
     KParams kp;
     kp.src = src;
     kp.out = out;
@@ -127,9 +149,141 @@ static int launch(DevState &d, const WorkSrc &src, double tol, const tw_opts &o,
     kp.slot_bytes = slot_bytes;
     kp.cap = cap;
     kp.tol = tol;
+    kp.chunk = cfg.chunk < 1 ? 1 : cfg.chunk;
     kp.counter = d.counter;
-    if ((e = lf((unsigned)blocks, st, kp)) != cudaSuccess) return cuda_fail(e);
+    bool graphed = false;
+    if (use_graph && st != nullptr) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaMemsetAsync(d.counter, 0, 6 * sizeof(unsigned long long), st);
+            cudaError_t e2 = lf((unsigned)blocks, st, kp);
+            e = cudaStreamEndCapture(st, &g);
+            if (e == cudaSuccess && e1 == cudaSuccess && e2 == cudaSuccess) {
+                bool ok = false;
+                if (d.graph) {
+                    cudaGraphExecUpdateResultInfo info;
+                    ok = cudaGraphExecUpdate(d.graph, g, &info) == cudaSuccess;
+                    if (!ok) { (void)cudaGetLastError(); cudaGraphExecDestroy(d.graph); d.graph = nullptr; }
+                }
+                if (!ok) ok = cudaGraphInstantiate(&d.graph, g, 0) == cudaSuccess;
+                if (ok && cudaGraphLaunch(d.graph, st) == cudaSuccess) graphed = true;
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        (void)cudaGetLastError();
+    }
+    if (!graphed) {
+        if ((e = cudaMemsetAsync(d.counter, 0, 6 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_fail(e);
+        if ((e = lf((unsigned)blocks, st, kp)) != cudaSuccess) return cuda_fail(e);
+    }
     if ((e = cudaEventRecord(d.last, st)) != cudaSuccess) return cuda_fail(e);
+    return TW_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// Chooses the launch shape by timing a calibration sub-sample (every k-th
+// position, about 5% of the call, at least 16 positions per resident warp and
+// at most 65536) for every
+// candidate, and caches the fastest per (GPU name, precision, tolerance
+// decade, workload kind) in memory and in a small text file
+// ($TW_AUTOTUNE_CACHE, default $HOME/.cache/twinkle_gb300_autotune.txt).
+// The samples per iteration it picks change the limb sampling, so results
+// differ from an untuned call within the tolerance.
+
+static std::map<std::string, LaunchCfg> g_tune;
+static bool g_tune_loaded = false;
+
+static std::string tune_path() {
+    const char *p = getenv("TW_AUTOTUNE_CACHE");
+    if (p && *p) return p;
+    const char *h = getenv("HOME");
+    return std::string(h && *h ? h : "/tmp") + "/.cache/twinkle_gb300_autotune.txt";
+}
+
+static void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    FILE *f = fopen(tune_path().c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        char *bar = strrchr(line, '|');
+        if (!bar) continue;
+        LaunchCfg c;
+        if (sscanf(bar + 1, "%d %d %d", &c.spl, &c.ctas, &c.chunk) != 3) continue;
+        if (c.spl != 1 && c.spl != 2 && c.spl != 4) continue;
+        *bar = 0;
+        g_tune[line] = c;
+    }
+    fclose(f);
+}
+
+static void tune_save() {
+    std::string path = tune_path();
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // may exist
+    FILE *f = fopen(path.c_str(), "w");
+    if (!f) return;
+    for (auto &kv : g_tune) fprintf(f, "%s|%d %d %d\n", kv.first.c_str(), kv.second.spl, kv.second.ctas, kv.second.chunk);
+    fclose(f);
+}
+
+static std::string tune_key(const DevState &d, int prec, double tol, int kind) {
+    char buf[400];
+    snprintf(buf, sizeof(buf), "%s;prec=%d;tol=1e%d;kind=%d", d.name, prec, (int)floor(log10(tol) + 1e-9), kind);
+    return buf;
+}
+
+static int autotune(DevState &d, const WorkSrc &src, double tol, int prec, int max_samples, cudaStream_t st,
+                    LaunchCfg *best) {
+    tune_load();
+    const std::string key = tune_key(d, prec, tol, src.kind);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) { *best = it->second; return TW_OK; }
+    // the sub-sample must give every resident warp a dozen positions or more,
+    // otherwise the timing measures the tail of the launch, not its throughput
+    const int64_t warps = (int64_t)d.nsm * 2 * WPB;
+    if (src.n < 8 * warps) return TW_OK;  // too small to time reliably: keep the defaults
+    int64_t ncal = src.n / 20;
+    if (ncal < 16 * warps) ncal = 16 * warps;
+    if (ncal > 65536) ncal = 65536;
+    if (ncal > src.n) ncal = src.n;
+    const int64_t stride = (src.n + ncal - 1) / ncal;
+    WorkSrc cal = src;
+    cal.stride = stride;
+    cal.n = (src.n + stride - 1) / stride;
+    int rc = grow(&d.calib, &d.calib_bytes, (size_t)cal.n * 8);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+    float best_ms = 3.0e38f;
+    const int spls[3] = {1, 2, 4};
+    const int ctass[2] = {1, 0};
+    const int chunks[2] = {1, 4};
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 2; b++)
+            for (int c = 0; c < 2; c++) {
+                const LaunchCfg cfg = {spls[a], ctass[b], chunks[c]};
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; rep++) {  // first run warms the arena and caches
+                    cudaEventRecord(e0, st);
+                    rc = launch(d, cal, tol, prec, max_samples, cfg, false, (double *)d.calib, nullptr, nullptr,
+                                nullptr, st);
+                    if (rc) break;
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = TW_ECUDA; break; }
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (rc) break;
+                if (ms < best_ms) { best_ms = ms; *best = cfg; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    g_tune[key] = *best;
+    tune_save();
     return TW_OK;
 }
 
@@ -164,10 +318,13 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     if (o.nsamp_out && is_device_ptr(o.nsamp_out) != dev) return TW_EINVAL;
     if (o.pos_status && is_device_ptr(o.pos_status) != dev) return TW_EINVAL;
     const void *din[4];
+    LaunchCfg cfg = {o.samples_per_iter / 32, 0, 1};
     if (dev) {
         for (int i = 0; i < c.nin; i++) din[i] = c.in[i];
         WorkSrc src = bind(din);
-        return launch(d, src, tol, o, out, o.err_out, o.nsamp_out, o.pos_status, st);
+        if (o.autotune && (rc = autotune(d, src, tol, o.precision, o.max_samples, st, &cfg))) return rc;
+        return launch(d, src, tol, o.precision, o.max_samples, cfg, o.use_graph != 0, out, o.err_out, o.nsamp_out,
+                      o.pos_status, st);
     }
     // host pointers: stage inputs and outputs through device memory
     size_t off[4], total = 0;
@@ -190,7 +347,9 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     double *derr = o.err_out ? (double *)(d.stage + o_err) : nullptr;
     int32_t *dns = o.nsamp_out ? (int32_t *)(d.stage + o_ns) : nullptr;
     int8_t *dps = (int8_t *)(d.stage + o_ps);
-    if ((rc = launch(d, src, tol, o, dout, derr, dns, dps, st))) return rc;
+    if (o.autotune && (rc = autotune(d, src, tol, o.precision, o.max_samples, st, &cfg))) return rc;
+    if ((rc = launch(d, src, tol, o.precision, o.max_samples, cfg, o.use_graph != 0, dout, derr, dns, dps, st)))
+        return rc;
     int8_t *hps = o.pos_status;
     int8_t *tmp_ps = nullptr;
     if (!hps) { tmp_ps = new int8_t[c.n]; hps = tmp_ps; }
@@ -235,7 +394,7 @@ int tw_mag_ex(double s, double q, double rho, const double *y1, const double *y2
     return run_call(c, rel_tol, opts, out, [&](const void **din) {
         WorkSrc w;
         memset(&w, 0, sizeof(w));
-        w.kind = 0; w.n = n; w.s = s; w.q = q; w.rho = rho;
+        w.kind = 0; w.n = n; w.s = s; w.q = q; w.rho = rho; w.stride = 1;
         w.y1 = (const double *)din[0];
         w.y2 = (const double *)din[1];
         return w;
@@ -260,7 +419,7 @@ int tw_lightcurve_ex(double s, double q, double rho, double u0, double alpha, do
     return run_call(c, rel_tol, opts, out, [&](const void **din) {
         WorkSrc w;
         memset(&w, 0, sizeof(w));
-        w.kind = 1; w.n = n; w.s = s; w.q = q; w.rho = rho;
+        w.kind = 1; w.n = n; w.s = s; w.q = q; w.rho = rho; w.stride = 1;
         w.u0 = u0; w.alpha = alpha; w.t0 = t0; w.tE = tE;
         w.times = (const double *)din[0];
         return w;
@@ -298,7 +457,7 @@ int tw_lightcurve_batch(const double *params, const int64_t *offsets, const doub
     return run_call(c, rel_tol, opts, out, [&](const void **din) {
         WorkSrc w;
         memset(&w, 0, sizeof(w));
-        w.kind = 2; w.n = total;
+        w.kind = 2; w.n = total; w.stride = 1;
         w.params = (const double *)din[0];
         w.offsets = (const int64_t *)din[1];
         w.times = (const double *)din[2];

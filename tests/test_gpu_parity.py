@@ -164,3 +164,27 @@ def test_device_reciprocal_against_ieee_division():
     """The kernels' FP64 reciprocal (hardware approximation + two Newton-Raphson
     steps) stays within a few ulp of IEEE division over 1e-300..1e300."""
     assert P.selftest_rcp() <= 4.5e-16
+
+
+def test_autotuned_and_graph_replayed_batch(tmp_path, monkeypatch):
+    """The autotuned launch shape and the CUDA-graph replay give results within
+    the tolerance of the oracle on the sampled batch points; a second call
+    reuses the cached shape and the graph."""
+    monkeypatch.setenv("TW_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    full_p, full_o, full_t = W.batch_lightcurves()
+    rows = load("batch_lightcurves.txt")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pd = torch.as_tensor(full_p, device="cuda")
+        od = torch.as_tensor(full_o, device="cuda")
+        td = dev(full_t)
+        for _ in range(2):
+            mu = P.lightcurve_batch(pd, od, td, rel_tol=1e-4, precision=P.PREC_MIXED, autotune=True, use_graph=True,
+                                    stream=stream)
+            stream.synchronize()
+            got = mu.cpu().numpy()
+            idx = np.array([int(r[1]) for r in rows])
+            ref = np.array([float(r[3]) for r in rows])
+            ok = np.array([int(r[4]) == 0 for r in rows])
+            assert rel_err(got[idx][ok], ref[ok]).max() <= TOL
+    assert (tmp_path / "tune.txt").exists()
