@@ -146,6 +146,14 @@ int tw_lightcurve_batch(const double *params, const int64_t *offsets, const doub
 int tw_mag_noalloc(double s, double q, double rho, const double *y1, const double *y2, int64_t n,
                    double rel_tol, double *out, int precision, int max_samples, void *stream);
 
+/* C[M][N] = A[M][K] . B[N][K]^T on the tensor cores (tcgen05.mma, BF16
+ * inputs, FP32 accumulation and output), the GEMM of the MLP surrogate; the
+ * paper has no counterpart.  A, B (bf16, row-major, K contiguous) and C
+ * (float32, row-major) are device pointers; M and N multiples of 128, K a
+ * multiple of 64.  Synchronous on `stream`.  TW_ETIMEOUT if a bounded
+ * device-side wait gave up (C is then undefined). */
+int tw_gemm_bf16(const void *A, const void *B, int M, int N, int K, float *C, void *stream);
+
 /* Text of a return code (TW_OK, TW_E*, TW_WCAP). */
 const char *tw_status_str(int code);
 

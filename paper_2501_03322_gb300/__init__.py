@@ -89,6 +89,8 @@ def lib():
             L.tw_selftest.restype = I
             L.tw_mag_noalloc.argtypes = [d, d, d, P, P, i64, d, P, I, I, P]
             L.tw_mag_noalloc.restype = I
+            L.tw_gemm_bf16.argtypes = [P, P, I, I, I, P, P]
+            L.tw_gemm_bf16.restype = I
             _lib = L
     return _lib
 
@@ -166,6 +168,19 @@ def last_launch_work() -> dict:
     a = np.zeros(5, np.int64)
     _check(lib().tw_last_launch_work(a.ctypes.data_as(ctypes.c_void_p)))
     return dict(samples=int(a[0]), sweeps64=int(a[1]), sweeps32=int(a[2]), edges=int(a[3]), newton64=int(a[4]))
+
+
+def gemm_bf16(A, B, out=None, stream=None):
+    """C = A @ B.T on the tensor cores (tw_gemm_bf16); A [M, K], B [N, K] bf16 CUDA tensors."""
+    import torch
+
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    st = _stream_of(A, stream)
+    _check(lib().tw_gemm_bf16(_ptr(A.contiguous()), _ptr(B.contiguous()), M, N, K, _ptr(out), st))
+    return out
 
 
 def selftest_rcp() -> float:
