@@ -71,6 +71,9 @@ def workload(name):
         y1, y2 = W.stress_positions()
         return dict(kind="mag", name="stress_resonant_1e6", s=c["s"], q=c["q"], rho=c["rho"], y1=y1, y2=y2,
                     rel_tol=c["rel_tol"], n=y1.size)
+    if name == "surrogate":
+        return dict(kind="surrogate", name="surrogate_fallback_1e7", n=10_000_000, ntrain=10_000_000, epochs=4,
+                    seed_train=0, seed_query=1, rel_tol=1e-4, kappa=3.0)
     if name == "batch_lightcurves":
         params, offsets, times = W.batch_lightcurves()
         return dict(kind="batch", name="batch_lightcurves_4096", params=params, offsets=offsets, times=times,
@@ -175,13 +178,30 @@ def flops_of(work, mode):
     return f64, f32
 
 
+def surrogate_oracle_queries():
+    """Positions near caustics placed by the oracle (tests/golden/surrogate_queries.txt)."""
+    path = os.path.join(ROOT, "tests", "golden", "surrogate_queries.txt")
+    rows = [ln.split() for ln in open(path) if not ln.startswith("#") and ln.strip()]
+    return np.array([[float(v) for v in r[:5]] for r in rows])
+
+
 def cpu_oracle_sample(wl, k, seed=777):
     """Time the CPU oracle on k positions of the workload using every host core."""
+    import concurrent.futures as cf
+
     import oracle as O
     from paper_2501_03322_gb300 import workloads as W
 
-    idx = W.sample_indices(int(wl["n"]), k, seed=seed)
     cores = os.cpu_count() or 1
+    if wl["kind"] == "surrogate":
+        # one lens per query: spread the queries over the cores
+        a = surrogate_oracle_queries()
+        idx = W.sample_indices(len(a), k, seed=seed)
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(lambda r: O.mag(r[0], r[1], r[2], [r[3]], [r[4]], nthreads=1), a[idx]))
+        return len(idx), time.perf_counter() - t0, cores
+    idx = W.sample_indices(int(wl["n"]), k, seed=seed)
     t0 = time.perf_counter()
     if wl["kind"] == "mag":
         O.mag(wl["s"], wl["q"], wl["rho"], wl["y1"][idx], wl["y2"][idx], nthreads=cores)
@@ -227,11 +247,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="map_planetary",
-                    choices=["map_planetary", "lightcurve_central", "stress_resonant", "batch_lightcurves"])
+                    choices=["map_planetary", "lightcurve_central", "stress_resonant", "batch_lightcurves",
+                             "surrogate"])
     ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-sample", type=int, default=128, help="positions in the CPU oracle baseline sample")
     ap.add_argument("--ref-sample", type=int, default=24, help="positions per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-samples", type=int, default=0, help="surrogate workload: training positions")
+    ap.add_argument("--queries", type=int, default=0, help="surrogate workload: query positions")
     ap.add_argument("--autotune", action="store_true", help="let the library choose the launch shape")
     ap.add_argument("--graph", action="store_true", help="replay each launch from a CUDA graph")
     ap.add_argument("--limit", type=int, default=0,
@@ -241,6 +264,11 @@ def main():
     metric = "finite-source mags/sec at rel.err<=1e-4: surrogate+fallback vs plain, 1 GB300"
     unit = "mags/s"
     wl = workload(args.workload)
+    if wl["kind"] == "surrogate":
+        if args.train_samples:
+            wl["ntrain"] = args.train_samples
+        if args.queries:
+            wl["n"] = args.queries
     if args.limit and wl["kind"] == "mag" and args.limit < wl["n"]:
         from paper_2501_03322_gb300 import workloads as W
 
@@ -290,12 +318,26 @@ def main():
         def step():
             P.lightcurve(wl["s"], wl["q"], wl["rho"], wl["u0"], wl["alpha"], wl["t0"], wl["tE"], td,
                          rel_tol=wl["rel_tol"], out=outd, **kw)
-    else:
+    elif wl["kind"] == "batch":
         pd, od, td = D(wl["params"]), D(wl["offsets"], torch.int64), D(wl["times"])
         outd = torch.empty_like(td)
 
         def step():
             P.lightcurve_batch(pd, od, td, rel_tol=wl["rel_tol"], out=outd, **kw)
+    else:
+        wpath = os.path.join(ROOT, "paper_2501_03322_gb300", "_build",
+                             "surrogate_s%d_n%d_e%d.bin" % (wl["seed_train"], wl["ntrain"], wl["epochs"]))
+        t0 = time.perf_counter()
+        if not os.path.exists(wpath):
+            wl["train_stats"] = P.surrogate_train(wpath, wl["ntrain"], wl["seed_train"], wl["epochs"])
+        wl["train_s"] = time.perf_counter() - t0
+        qd = P.surrogate_sample(wl["seed_query"], wl["n"], device=dev)
+        outd = torch.empty(wl["n"], dtype=torch.float64, device=dev)
+        wl["nfb"] = []
+
+        def step(kappa=wl["kappa"]):
+            _, nf = P.surrogate_mag(wpath, *qd, rel_tol=wl["rel_tol"], kappa=kappa, precision=prec, out=outd)
+            wl["nfb"].append(nf)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
@@ -334,6 +376,22 @@ def main():
         t_step = float(tt.item())
         dist.barrier()
     value = world * wl["n"] / t_step
+    extra = {}
+    if wl["kind"] == "surrogate":
+        # plain contour integration of the same queries: every query falls back
+        nfb = list(wl["nfb"][-args.steps:])
+        pe = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        flush.zero_()
+        pe[0].record(stream)
+        step(kappa=1e30)
+        pe[1].record(stream)
+        pe[1].synchronize()
+        t_plain = pe[0].elapsed_time(pe[1]) / 1e3
+        extra = {"surrogate": {"fallback_fraction": sum(nfb) / (len(nfb) * wl["n"]),
+                               "plain_value": wl["n"] / t_plain, "plain_ms_per_step": t_plain * 1e3,
+                               "speedup_vs_plain": t_plain / t_step, "train_s": wl.get("train_s"),
+                               "train_stats": wl.get("train_stats"), "queries": wl["n"],
+                               "kappa": wl["kappa"]}}
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     if wl["kind"] == "mag":
@@ -353,6 +411,14 @@ def main():
         def e2e_step():
             P.lightcurve(wl["s"], wl["q"], wl["rho"], wl["u0"], wl["alpha"], wl["t0"], wl["tE"], ht.numpy(),
                          rel_tol=wl["rel_tol"], precision=prec, autotune=args.autotune, out=hout.numpy())
+    elif wl["kind"] == "surrogate":
+        hq = [t.cpu().pin_memory() for t in qd]
+        hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()
+        h2d, d2h = 40 * wl["n"], 8 * wl["n"]
+
+        def e2e_step():
+            P.surrogate_mag(wpath, *[t.numpy() for t in hq], rel_tol=wl["rel_tol"], kappa=wl["kappa"],
+                            precision=prec, out=hout.numpy())
     else:
         hp = torch.from_numpy(wl["params"]).pin_memory()
         ho = torch.from_numpy(wl["offsets"]).pin_memory()
@@ -395,12 +461,14 @@ def main():
             "config": cfg, "roofline": roof, "clocks": clocks,
             "e2e": {"value": world * wl["n"] / t_e2e, "unit": unit, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps, "wall_s_timed": wall,
+            "gpu_launches": args.steps * (1 + 6 * ((wl["n"] + (1 << 20) - 1) >> 20) if wl["kind"] == "surrogate" else 1),
+            "wall_s_timed": wall,
             "work": {"samples_per_position": work["samples"] / (args.steps * wl["n"]),
                      "fp64_sweeps_per_sample": work["sweeps64"] / max(work["samples"], 1),
                      "fp32_sweeps_per_sample": work["sweeps32"] / max(work["samples"], 1),
                      "fp64_newton_per_sample": work["newton64"] / max(work["samples"], 1),
                      "edges_per_sample": work["edges"] / max(work["samples"], 1)}}
+    line.update(extra)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, cores = cpu_oracle_sample(wl, args.cpu_sample)
         line["cpu_baseline"] = {"value": n / dt, "unit": unit, "cores": cores, "kind": "oracle",

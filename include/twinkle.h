@@ -146,6 +146,40 @@ int tw_lightcurve_batch(const double *params, const int64_t *offsets, const doub
 int tw_mag_noalloc(double s, double q, double rho, const double *y1, const double *y2, int64_t n,
                    double rel_tol, double *out, int precision, int max_samples, void *stream);
 
+/* MLP surrogate (not in the paper; a systems pattern of this library).  A
+ * BF16 network 5 -> 256 -> 256 -> 256 -> 256 -> 2 maps (log10 s, log10 q,
+ * log10 rho, y1, y2) to r = ln(mu / mu_ps) and l = ln(sigma), mu_ps being the
+ * point-source magnification at the source centre (images of Eq. 6, parity
+ * and Jacobian of Eq. 7); the hidden layers run on the tensor cores.
+ *
+ * tw_surrogate_train draws nsamples positions near caustics (a random point of
+ * a random branch of the caustic of a random lens with log10 s ~ U[-0.5, 0.5],
+ * log10 q ~ U[-5, -1], log10 rho ~ U[-4, -2], displaced uniformly within three
+ * times that branch's size) from `seed`, labels those that are not flagged as
+ * near a caustic with the contour integrator (FP64, rel_tol 1e-5), trains for
+ * `epochs` epochs (Gaussian likelihood, Adam, batch 4096) and writes the
+ * weights file (magic, shapes, standardisation, FP32 weights, checksum).
+ * stats (optional, [5]): positions drawn, positions labelled, training rows,
+ * mean loss of the last epoch, spread of the targets.  Synchronous. */
+int tw_surrogate_train(const char *weights_path, int64_t nsamples, uint64_t seed, int epochs, double *stats,
+                       const tw_opts *opts);
+
+/* Surrogate magnification of n queries with per-query lens and source radius
+ * (arrays s, q, rho, y1, y2; host or device, all of one kind).  A query falls
+ * back to contour integration (one persistent launch over the fallbacks, with
+ * opts->precision and opts->max_samples) when it is flagged as near a caustic
+ * (the image count differs between the centre and any of 8 points 2 rho away,
+ * or min |J| < 0.1 at the centre) or when kappa * sigma > rel_tol.  out[i]
+ * receives mu; *n_fallback (optional) the number of fallbacks.  Synchronous. */
+int tw_surrogate_mag(const char *weights_path, const double *s, const double *q, const double *rho,
+                     const double *y1, const double *y2, int64_t n, double rel_tol, double kappa, double *out,
+                     int64_t *n_fallback, const tw_opts *opts);
+
+/* The training-position sampler of tw_surrogate_train, on its own: n seeded
+ * positions near caustics into device arrays (asynchronous on `stream`). */
+int tw_surrogate_sample(uint64_t seed, int64_t n, double *s, double *q, double *rho, double *y1, double *y2,
+                        void *stream);
+
 /* C[M][N] = A[M][K] . B[N][K]^T on the tensor cores (tcgen05.mma, BF16
  * inputs, FP32 accumulation and output), the GEMM of the MLP surrogate; the
  * paper has no counterpart.  A, B (bf16, row-major, K contiguous) and C

@@ -91,6 +91,12 @@ def lib():
             L.tw_mag_noalloc.restype = I
             L.tw_gemm_bf16.argtypes = [P, P, I, I, I, P, P]
             L.tw_gemm_bf16.restype = I
+            L.tw_surrogate_train.argtypes = [ctypes.c_char_p, i64, ctypes.c_uint64, I, P, P]
+            L.tw_surrogate_train.restype = I
+            L.tw_surrogate_mag.argtypes = [ctypes.c_char_p, P, P, P, P, P, i64, d, d, P, P, P]
+            L.tw_surrogate_mag.restype = I
+            L.tw_surrogate_sample.argtypes = [ctypes.c_uint64, i64, P, P, P, P, P, P]
+            L.tw_surrogate_sample.restype = I
             _lib = L
     return _lib
 
@@ -181,6 +187,39 @@ def gemm_bf16(A, B, out=None, stream=None):
     st = _stream_of(A, stream)
     _check(lib().tw_gemm_bf16(_ptr(A.contiguous()), _ptr(B.contiguous()), M, N, K, _ptr(out), st))
     return out
+
+
+def surrogate_train(path, nsamples=1_000_000, seed=0, epochs=4, stream=None):
+    """Train the MLP surrogate (tw_surrogate_train); returns its statistics."""
+    st = np.zeros(5)
+    o = make_opts(stream=getattr(stream, "cuda_stream", stream))
+    _check(lib().tw_surrogate_train(str(path).encode(), int(nsamples), int(seed), int(epochs),
+                                    st.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o)))
+    return dict(drawn=int(st[0]), labelled=int(st[1]), rows=int(st[2]), loss=float(st[3]), target_std=float(st[4]))
+
+
+def surrogate_sample(seed, n, device="cuda"):
+    """n seeded query positions near caustics (tw_surrogate_sample): five CUDA tensors."""
+    import torch
+
+    a = [torch.empty(int(n), dtype=torch.float64, device=device) for _ in range(5)]
+    st = torch.cuda.current_stream(a[0].device).cuda_stream
+    _check(lib().tw_surrogate_sample(int(seed), int(n), *[_ptr(t) for t in a], st))
+    return a
+
+
+def surrogate_mag(path, s, q, rho, y1, y2, rel_tol=1e-4, kappa=3.0, precision=PREC_FP64, max_samples=4096, out=None,
+                  stream=None):
+    """Surrogate magnification with contour fallback (tw_surrogate_mag); returns (out, n_fallback)."""
+    arrs = [_prep(a) for a in (s, q, rho, y1, y2)]
+    n = int(arrs[0].shape[0])
+    if out is None:
+        out = _alloc_like(arrs[0], n, np.float64, "float64")
+    nf = ctypes.c_int64(0)
+    o = make_opts(precision, 64, max_samples, _stream_of(arrs[0], stream))
+    _check(lib().tw_surrogate_mag(str(path).encode(), *[_ptr(a) for a in arrs], n, rel_tol, kappa, _ptr(out),
+                                  ctypes.byref(nf), ctypes.byref(o)))
+    return out, int(nf.value)
 
 
 def selftest_rcp() -> float:

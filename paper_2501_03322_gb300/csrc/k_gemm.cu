@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include "../../include/twinkle.h"
+#include "gemm.cuh"
 #include "kernels.cuh"
 #include "mma.cuh"
 
@@ -24,17 +25,6 @@ constexpr int GB_M = 128, GB_N = 128, GB_K = 64;
 constexpr uint32_t GEMM_WAIT_LIMIT = 1u << 26;  // polls (~0.1-1 s) before a wait is declared hung
 constexpr size_t GEMM_STAGE_BYTES = 2 * 16384;   // A and B tiles of one stage
 constexpr size_t GEMM_SMEM = 1024 + 2 * GEMM_STAGE_BYTES + 64;
-
-struct GemmArgs {
-    const __nv_bfloat16 *A;  // [M][K]
-    const __nv_bfloat16 *B;  // [N][K]
-    int M, N, K;
-    float *C;                // optional FP32 output [M][N]
-    __nv_bfloat16 *Cb;       // optional BF16 output [M][N]
-    const float *bias;       // optional [N]
-    int relu;                // apply max(x, 0) after the bias
-    int *err;                // set to 1 if a bounded wait gave up
-};
 
 __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(GemmArgs g) {
     extern __shared__ uint8_t smem_raw[];

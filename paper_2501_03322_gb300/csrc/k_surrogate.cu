@@ -1,0 +1,899 @@
+// k_surrogate.cu -- BF16 MLP surrogate of the finite-source magnification,
+// with contour-integration fallback; training and inference.
+//
+// The network maps x = (log10 s, log10 q, log10 rho, y1, y2) (standardised)
+// through 5 -> 256 -> 256 -> 256 -> 256 -> 2 (ReLU) to (r, l): r is the
+// logarithm of the ratio of the finite-source magnification to the
+// point-source magnification at the source centre, l = ln(sigma) its predicted
+// uncertainty, so mu = mu_ps exp(r).  Learning the finite-source correction on
+// top of the point-source value keeps the BF16 network's errors on a quantity
+// that is small away from caustics.  The three 256 x 256 layers run on the
+// tensor cores (k_gemm.cu, BF16 weights and activations, FP32 accumulation);
+// the 5 -> 256 input layer and the 256 -> 2 head run in FP32 on CUDA cores.
+//
+// Inference: per query, the point-source images at the centre (Eq. 6
+// quintic, FP32 Aberth + FP64 Newton, residual ghost test, mu_ps = sum 1/|J|),
+// a near-caustic flag (the image count differs between the centre and any of
+// 8 points at distance 2 rho, or min |J| < 0.1 at the centre), the MLP, and
+// the fallback decision: flagged, or kappa * sigma > rel_tol.  Fallback
+// queries are integrated by the contour kernel in one persistent launch.
+//
+// Training: positions are drawn near caustics (a random point of a random
+// branch of the caustic, displaced uniformly in a disc of three times that
+// branch's bounding-box size), labelled by the contour integrator (FP64 mode),
+// and the network is fitted by the Gaussian negative log-likelihood of r with
+// Adam on FP32 master weights.  Flagged (near-caustic) samples are left out of
+// training: they always fall back.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/twinkle.h"
+#include "gemm.cuh"
+#include "kernels.cuh"
+
+namespace tw {
+
+constexpr int SH = 256;   // hidden width
+constexpr int SNIN = 5;   // inputs
+constexpr int SXP = 8;    // padded input row (floats)
+// offsets in the FP32 parameter blob (weights stored [out][in])
+constexpr int OW1 = 0, OB1 = OW1 + SH * SNIN;
+constexpr int OW2 = OB1 + SH, OB2 = OW2 + SH * SH;
+constexpr int OW3 = OB2 + SH, OB3 = OW3 + SH * SH;
+constexpr int OW4 = OB3 + SH, OB4 = OW4 + SH * SH;
+constexpr int OW5 = OB4 + SH, OB5 = OW5 + 2 * SH;
+constexpr int NPAR = OB5 + 2;
+constexpr int OWH[3] = {OW2, OW3, OW4};
+constexpr int OBH[3] = {OB2, OB3, OB4};
+
+struct SurNorm {
+    float mean[SNIN], inv_std[SNIN];
+};
+
+// ------------------------------------------------------------ random numbers
+// splitmix64 (Steele, Lea & Flood 2014): a counter-based 64-bit generator.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t &x) {
+    x += 0x9E3779B97F4A7C15ull;
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double u01(uint64_t &st) { return (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0); }
+
+// ------------------------------------------------- training-position sampler
+// Critical curve (f'(z) = e^{i phi}, Eq. 7 with |f'| = 1) in the secondary's
+// frame eta = z - z2:  e eta^4 + 2 s e eta^3 + (s^2 e - 1) eta^2 - 2 s m2 eta - m2 s^2 = 0.
+constexpr int NPHI = 64;
+
+__global__ void sur_sample_kernel(uint64_t seed, int64_t n, double *S, double *Q, double *RHO, double *Y1,
+                                  double *Y2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t st = seed * 0xD1B54A32D192ED03ull + (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    (void)splitmix64(st);
+    const double s = exp10(-0.5 + u01(st));
+    const double q = exp10(-5.0 + 4.0 * u01(st));
+    const double rho = exp10(-4.0 + 2.0 * u01(st));
+    const double m2 = q / (1.0 + q), m1 = 1.0 - m2;
+    const int kb = (int)(u01(st) * NPHI) % NPHI;
+    const int bb = (int)(u01(st) * 4.0) & 3;
+    cxd z[4];
+    const double r0 = 1.0 + s;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        double sn, cs;
+        sincos(1.5707963267948966 * k + 0.3, &sn, &cs);
+        z[k] = {-0.5 * s + r0 * cs, r0 * sn};
+    }
+    double bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
+    cxd chosen = {0.0, 0.0};
+    for (int k = 0; k < NPHI; k++) {
+        double sn, cs;
+        sincos(6.283185307179586 * k / NPHI, &sn, &cs);
+        const cxd e = {cs, sn};
+        cxd c[5];
+        c[4] = e;
+        c[3] = (2.0 * s) * e;
+        c[2] = {s * s * cs - 1.0, s * s * sn};
+        c[1] = {-2.0 * s * m2, 0.0};
+        c[0] = {-m2 * s * s, 0.0};
+        // Aberth-Ehrlich iteration warm-started from the previous angle, so each
+        // root index follows one branch of the critical curve
+        for (int it = 0; it < (k == 0 ? 200 : 60); it++) {
+            cxd S4[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) S4[a] = {0.0, 0.0};
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = a + 1; b < 4; b++) {
+                    const cxd r = inv(z[a] - z[b]);
+                    S4[a] = S4[a] + r;
+                    S4[b] = S4[b] - r;
+                }
+            double wmax = 0.0, zmax = 0.0;
+            cxd w[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                cxd p = c[4], d = {0.0, 0.0};
+#pragma unroll
+                for (int t = 3; t >= 0; t--) {
+                    d = d * z[a] + p;
+                    p = p * z[a] + c[t];
+                }
+                w[a] = cdiv(p, d - p * S4[a]);
+                wmax = fmax(wmax, norm2(w[a]));
+                zmax = fmax(zmax, norm2(z[a]));
+            }
+#pragma unroll
+            for (int a = 0; a < 4; a++) z[a] = z[a] - w[a];
+            if (wmax <= 1e-26 * (zmax + 1e-30)) break;
+        }
+        cxd eta = z[0];
+#pragma unroll
+        for (int a = 1; a < 4; a++)
+            if (a == bb) eta = z[a];
+        const cxd g = m1 * inv(cxd{eta.x + s, eta.y}) + m2 * inv(eta);
+        const cxd y = eta - conj(g);  // caustic point, secondary frame
+        bx0 = fmin(bx0, y.x);
+        bx1 = fmax(bx1, y.x);
+        by0 = fmin(by0, y.y);
+        by1 = fmax(by1, y.y);
+        if (k == kb) chosen = y;
+    }
+    const double wdt = fmax(bx1 - bx0, by1 - by0);
+    const double rr = 3.0 * wdt * sqrt(u01(st));
+    double sn, cs;
+    sincos(6.283185307179586 * u01(st), &sn, &cs);
+    S[i] = s;
+    Q[i] = q;
+    RHO[i] = rho;
+    Y1[i] = chosen.x + rr * cs + s * m1;  // back to the centre-of-mass frame (z2 = s m1)
+    Y2[i] = chosen.y + rr * sn;
+}
+
+// ------------------------------------------------ point-source images, flag
+// Images of a point source at y (secondary frame): FP32 Aberth from z, then
+// (fp64 = true) two FP64 Newton steps.  Returns the image count by the
+// residual pair test (Sec. 2.4.1) and, for the real images, sum 1/|J| and
+// min |J| (Eq. 7).
+template <bool FP64>
+__device__ int point_images(const LensK &L, cxd y, cxd z[5], double &mu_ps, double &minJ) {
+    cxd c[6];
+    eq6_coeffs(L.s, L.m2, y, c);
+    float ca[6];
+    abs_coeffs(c, ca);
+    const float cm = fmaxf(fmaxf(fmaxf(ca[0], ca[1]), fmaxf(ca[2], ca[3])), fmaxf(ca[4], ca[5]));
+    const double sc = 1.0 / (double)cm;
+    cxf cf[6];
+    float caf[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        cf[k] = to_f(sc * c[k]);
+        caf[k] = ca[k] / cm;
+    }
+    cxf zf[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) zf[i] = to_f(z[i]);
+    float dpa[5];
+    for (int it = 0; it < 100; it++)
+        if (aberth_sweep<float>(cf, caf, zf, dpa, 2e-6f, 6e-8f)) break;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        z[i] = to_d(zf[i]);
+        if (FP64) {
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                cxd p, d;
+                horner(c, z[i], p, d);
+                z[i] = z[i] - cdiv(p, d);
+            }
+        }
+    }
+    double aR[5], J[5];
+    cxd R[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const cxd d1 = inv(cxd{z[i].x + L.s, z[i].y}), d2 = inv(z[i]);
+        R[i] = y - z[i] + conj(L.m1 * d1 + L.m2 * d2);
+        aR[i] = norm2(R[i]);
+        const cxd f1 = L.m1 * (d1 * d1) + L.m2 * (d2 * d2);
+        J[i] = 1.0 - norm2(f1);
+    }
+    int r3 = 0, r4 = 0, r5 = 0;
+    int rank[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < 5; j++)
+            if (j != i) r += (aR[j] < aR[i]) || (aR[j] == aR[i] && j < i);
+        rank[i] = r;
+        if (r == 2) r3 = i;
+        if (r == 3) r4 = i;
+        if (r == 4) r5 = i;
+    }
+    cxd R45 = {0.0, 0.0};
+    double a3 = 0, a4 = 0, a5 = 0;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        if (i == r4 || i == r5) R45 = R45 + R[i];
+        if (i == r3) a3 = aR[i];
+        if (i == r4) a4 = aR[i];
+        if (i == r5) a5 = aR[i];
+    }
+    const int count = (norm2(R45) < 1e-4 * a5 && a4 > 100.0 * a3) ? 3 : 5;
+    mu_ps = 0.0;
+    minJ = 1e300;
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+        if (rank[i] < count) {
+            mu_ps += 1.0 / fabs(J[i]);
+            minJ = fmin(minJ, fabs(J[i]));
+        }
+    return count;
+}
+
+// Raw features, point-source magnification and near-caustic flag per query.
+__global__ void sur_features_kernel(int64_t n, const double *S, const double *Q, const double *RHO, const double *Y1,
+                                    const double *Y2, float *X, double *MUPS, uint8_t *FLAG) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = S[i], q = Q[i], rho = RHO[i], y1 = Y1[i], y2 = Y2[i];
+    float *x = X + i * SXP;
+    x[0] = (float)log10(s);
+    x[1] = (float)log10(q);
+    x[2] = (float)log10(rho);
+    x[3] = (float)y1;
+    x[4] = (float)y2;
+    x[5] = x[6] = x[7] = 0.f;
+    const bool ok = s > 0 && q > 0 && rho > 0 && isfinite(s) && isfinite(q) && isfinite(rho) && isfinite(y1) &&
+                    isfinite(y2);
+    if (!ok) { MUPS[i] = __longlong_as_double(0x7ff8000000000000ll); FLAG[i] = 1; return; }
+    if (q > 1.0) { q = 1.0 / q; y1 = -y1; }  // mass-swap symmetry (see kernels.cuh)
+    LensK L;
+    L.s = s;
+    L.m1 = 1.0 / (1.0 + q);
+    L.m2 = q * L.m1;
+    L.rho = rho;
+    const cxd y0 = {y1 - s * L.m1, y2};
+    cxd z[5];
+    initial_roots(s, y0, z);
+    double mu, minJ;
+    const int c0 = point_images<true>(L, y0, z, mu, minJ);
+    bool flag = !(isfinite(mu) && mu >= 1.0 - 1e-3) || minJ < 0.1;
+    // the image count at 8 points 2 rho away must equal the centre's
+    for (int k = 0; k < 8 && !flag; k++) {
+        double sn, cs;
+        sincos(0.7853981633974483 * k + 0.2, &sn, &cs);
+        const cxd yk = {y0.x + 2.0 * rho * cs, y0.y + 2.0 * rho * sn};
+        cxd zk[5] = {z[0], z[1], z[2], z[3], z[4]};
+        double m, mj;
+        if (point_images<false>(L, yk, zk, m, mj) != c0) flag = true;
+    }
+    MUPS[i] = mu;
+    FLAG[i] = flag ? 1 : 0;
+}
+
+// ------------------------------------------------------------- MLP kernels
+// Layer 1 (5 -> 256, ReLU) on CUDA cores; optionally the standardised inputs.
+__global__ void sur_layer1_kernel(int64_t rows, const float *X, const float *P, SurNorm nrm, __nv_bfloat16 *H1,
+                                  float *XS) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * SH) return;
+    const int64_t r = t / SH;
+    const int o = (int)(t % SH);
+    float xs[SNIN];
+#pragma unroll
+    for (int k = 0; k < SNIN; k++) xs[k] = (X[r * SXP + k] - nrm.mean[k]) * nrm.inv_std[k];
+    float h = P[OB1 + o];
+#pragma unroll
+    for (int k = 0; k < SNIN; k++) h = fmaf(P[OW1 + o * SNIN + k], xs[k], h);
+    H1[r * SH + o] = __float2bfloat16_rn(fmaxf(h, 0.f));
+    if (XS && o < SXP) XS[r * SXP + o] = o < SNIN ? xs[o] : 0.f;
+}
+
+// Head (256 -> 2) and fallback decision; one warp per query.
+__global__ void sur_head_infer_kernel(int64_t n, int64_t row0, const __nv_bfloat16 *H4, const float *P,
+                                      const double *MUPS, const uint8_t *FLAG, double tol, float kappa, double *OUT,
+                                      int32_t *LIST, unsigned long long *NLIST) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const uint4 v = *(const uint4 *)(H4 + w * SH + lane * 8);
+    const __nv_bfloat16 *h = (const __nv_bfloat16 *)&v;
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const float x = __bfloat162float(h[j]);
+        a = fmaf(P[OW5 + lane * 8 + j], x, a);
+        b = fmaf(P[OW5 + SH + lane * 8 + j], x, b);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        const int64_t g = row0 + w;
+        const float r = a + P[OB5], l = b + P[OB5 + 1];
+        const double mu = MUPS[g] * exp((double)r);
+        const bool fb = FLAG[g] || !(kappa * expf(l) <= (float)tol) || !isfinite(mu);
+        if (fb) {
+            const unsigned long long slot = atomicAdd(NLIST, 1ull);
+            LIST[slot] = (int32_t)g;
+            OUT[g] = __longlong_as_double(0x7ff8000000000000ll);
+        } else {
+            OUT[g] = mu;
+        }
+    }
+}
+
+// Head forward, Gaussian negative log-likelihood of the target t with weight
+// wt, its gradient with respect to the head outputs (DOUT), and the masked
+// gradient of the last hidden layer (G4 = dL/dh4 * [h4 > 0]); one warp per row.
+__global__ void sur_head_train_kernel(int B, const __nv_bfloat16 *H4, const float *P, const float *T, const float *WT,
+                                      float *DOUT, __nv_bfloat16 *G4, float *LOSS) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= B) return;
+    const uint4 v = *(const uint4 *)(H4 + (size_t)w * SH + lane * 8);
+    const __nv_bfloat16 *h = (const __nv_bfloat16 *)&v;
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const float x = __bfloat162float(h[j]);
+        a = fmaf(P[OW5 + lane * 8 + j], x, a);
+        b = fmaf(P[OW5 + SH + lane * 8 + j], x, b);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const float r = a + P[OB5];
+    const float l = fminf(fmaxf(b + P[OB5 + 1], -25.f), 5.f);
+    const float wt = WT[w] / (float)B;
+    const float d = T[w] - r, ie2 = expf(-2.f * l);
+    const float dr = -d * ie2 * wt, dl = (1.f - d * d * ie2) * wt;
+    if (lane == 0) {
+        DOUT[2 * w] = dr;
+        DOUT[2 * w + 1] = dl;
+        atomicAdd(LOSS, 0.5f * (d * d * ie2 + 2.f * l) * wt);
+    }
+    __nv_bfloat16 g[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int k = lane * 8 + j;
+        const float gv = dr * P[OW5 + k] + dl * P[OW5 + SH + k];
+        g[j] = __float2bfloat16_rn(__bfloat162float(h[j]) > 0.f ? gv : 0.f);
+    }
+    *(uint4 *)(G4 + (size_t)w * SH + lane * 8) = *(uint4 *)g;
+}
+
+// dW5 = DOUT^T H4, db5 = column sums of DOUT.
+__global__ void sur_head_wgrad_kernel(int B, const float *DOUT, const __nv_bfloat16 *H4, float *G) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * SH + 2) return;
+    float acc = 0.f;
+    if (t < 2 * SH) {
+        const int o = t / SH, k = t % SH;
+        for (int b = 0; b < B; b++) acc = fmaf(DOUT[2 * b + o], __bfloat162float(H4[(size_t)b * SH + k]), acc);
+        G[OW5 + t] = acc;
+    } else {
+        const int o = t - 2 * SH;
+        for (int b = 0; b < B; b++) acc += DOUT[2 * b + o];
+        G[OB5 + o] = acc;
+    }
+}
+
+// out[c][r] = in[r][c] for a R x C bf16 matrix (32 x 32 tiles).
+__global__ void transpose_bf16_kernel(int R, int C, const __nv_bfloat16 *in, __nv_bfloat16 *out) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < R && c < C) tile[k][threadIdx.x] = in[(size_t)r * C + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(size_t)c * R + r] = tile[threadIdx.x][k];
+    }
+}
+
+// G = DH * [H > 0] (bf16).
+__global__ void relu_mask_kernel(int64_t n, const float *DH, const __nv_bfloat16 *H, __nv_bfloat16 *G) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    G[i] = __float2bfloat16_rn(__bfloat162float(H[i]) > 0.f ? DH[i] : 0.f);
+}
+
+// out[c] = sum_r G[r][c] (bias gradient).
+__global__ void colsum_bf16_kernel(int B, const __nv_bfloat16 *Gm, float *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= SH) return;
+    float acc = 0.f;
+    for (int b = 0; b < B; b++) acc += __bfloat162float(Gm[(size_t)b * SH + c]);
+    out[c] = acc;
+}
+
+// Layer-1 gradients from DH1 (unmasked, fp32) and the standardised inputs.
+__global__ void sur_layer1_bwd_kernel(int B, const float *DH1, const __nv_bfloat16 *H1, const float *XS, float *G) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= SH) return;
+    float gw[SNIN] = {0.f, 0.f, 0.f, 0.f, 0.f}, gb = 0.f;
+    for (int b = 0; b < B; b++) {
+        const float g = __bfloat162float(H1[(size_t)b * SH + o]) > 0.f ? DH1[(size_t)b * SH + o] : 0.f;
+        gb += g;
+#pragma unroll
+        for (int k = 0; k < SNIN; k++) gw[k] = fmaf(g, XS[(size_t)b * SXP + k], gw[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < SNIN; k++) G[OW1 + o * SNIN + k] = gw[k];
+    G[OB1 + o] = gb;
+}
+
+__global__ void adam_kernel(int n, float *Pm, const float *G, float *M1, float *M2, float lr, float b1, float b2,
+                            float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float m = b1 * M1[i] + (1.f - b1) * g;
+    const float v = b2 * M2[i] + (1.f - b2) * g * g;
+    M1[i] = m;
+    M2[i] = v;
+    Pm[i] -= lr * (m * c1) / (sqrtf(v * c2) + 1e-8f);
+}
+
+// BF16 copies of the hidden-layer weights: forward ([out][in]) and transposed.
+__global__ void refresh_bf16_kernel(const float *Pm, __nv_bfloat16 *Wf, __nv_bfloat16 *Wt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * SH * SH) return;
+    const int l = t / (SH * SH), e = t % (SH * SH), o = e / SH, k = e % SH;
+    const __nv_bfloat16 v = __float2bfloat16_rn(Pm[(l == 0 ? OW2 : l == 1 ? OW3 : OW4) + e]);
+    Wf[(size_t)l * SH * SH + e] = v;
+    Wt[(size_t)l * SH * SH + (size_t)k * SH + o] = v;
+}
+
+// Targets r = ln(mu) - ln(mu_ps) and weights (0 for flagged or non-finite).
+__global__ void sur_targets_kernel(int64_t n, const double *MU, const double *MUPS, const uint8_t *FLAG, float *T,
+                                   float *WT) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = log(MU[i]) - log(MUPS[i]);
+    const bool ok = !FLAG[i] && isfinite(r);
+    T[i] = ok ? (float)r : 0.f;
+    WT[i] = ok ? 1.f : 0.f;
+}
+
+__global__ void compact_unflagged_kernel(int64_t n, const uint8_t *FLAG, int32_t *LIST, unsigned long long *NLIST) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || FLAG[i]) return;
+    LIST[atomicAdd(NLIST, 1ull)] = (int32_t)i;
+}
+
+// rows of X, T, WT selected by LIST, into dense training arrays
+__global__ void gather_train_kernel(int64_t m, const int32_t *LIST, const float *X, const float *T, const float *WT,
+                                    float *Xc, float *Tc, float *WTc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t j = LIST[i];
+#pragma unroll
+    for (int k = 0; k < SXP; k++) Xc[i * SXP + k] = X[j * SXP + k];
+    Tc[i] = T[j];
+    WTc[i] = WT[j];
+}
+
+// ------------------------------------------------------------------ host side
+
+static int cerr(cudaError_t e) {
+    if (e == cudaSuccess) return TW_OK;
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? TW_ENOMEM : TW_ECUDA;
+}
+
+static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Device buffers owned by one call (freed on scope exit).
+struct DevBufs {
+    std::vector<void *> p;
+    ~DevBufs() {
+        for (void *q : p) cudaFree(q);
+    }
+    template <typename T>
+    int get(T **out, size_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 256);
+        if (e != cudaSuccess) { (void)cudaGetLastError(); return TW_ENOMEM; }
+        p.push_back(q);
+        *out = (T *)q;
+        return TW_OK;
+    }
+};
+
+static uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *b = (const unsigned char *)data;
+    for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+static const char MAGIC[8] = {'T', 'W', 'M', 'L', 'P', '0', '0', '1'};
+
+// Weights file: magic, int32 {version 1, hidden, inputs, nparams}, the
+// standardisation (mean, 1/std), the FP32 parameters, FNV-1a checksum.
+static int save_model(const char *path, const std::vector<float> &P, const SurNorm &nrm) {
+    FILE *f = fopen(path, "wb");
+    if (!f) return TW_EINVAL;
+    const int32_t hdr[4] = {1, SH, SNIN, NPAR};
+    uint64_t h = fnv1a(MAGIC, 8);
+    h = fnv1a(hdr, sizeof(hdr), h);
+    h = fnv1a(&nrm, sizeof(nrm), h);
+    h = fnv1a(P.data(), P.size() * 4, h);
+    bool ok = fwrite(MAGIC, 8, 1, f) == 1 && fwrite(hdr, sizeof(hdr), 1, f) == 1 && fwrite(&nrm, sizeof(nrm), 1, f) == 1 &&
+              fwrite(P.data(), 4, P.size(), f) == P.size() && fwrite(&h, 8, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? TW_OK : TW_EINVAL;
+}
+
+static int load_model(const char *path, std::vector<float> &P, SurNorm &nrm) {
+    FILE *f = fopen(path, "rb");
+    if (!f) return TW_EINVAL;
+    char mg[8];
+    int32_t hdr[4];
+    uint64_t h = 0;
+    P.assign(NPAR, 0.f);
+    bool ok = fread(mg, 8, 1, f) == 1 && memcmp(mg, MAGIC, 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+              hdr[0] == 1 && hdr[1] == SH && hdr[2] == SNIN && hdr[3] == NPAR &&
+              fread(&nrm, sizeof(nrm), 1, f) == 1 && fread(P.data(), 4, NPAR, f) == (size_t)NPAR &&
+              fread(&h, 8, 1, f) == 1;
+    fclose(f);
+    if (!ok) return TW_EINVAL;
+    uint64_t c = fnv1a(MAGIC, 8);
+    c = fnv1a(hdr, sizeof(hdr), c);
+    c = fnv1a(&nrm, sizeof(nrm), c);
+    c = fnv1a(P.data(), P.size() * 4, c);
+    return c == h ? TW_OK : TW_EINVAL;
+}
+
+// Loaded model per device: FP32 parameters and BF16 copies of the hidden weights.
+struct Model {
+    std::string path;
+    float *P = nullptr;
+    __nv_bfloat16 *Wf = nullptr, *Wt = nullptr;
+    SurNorm nrm;
+};
+static std::mutex g_sm;
+static Model g_models[64];
+
+static int model_for(const char *path, cudaStream_t st, Model **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cerr(cudaErrorInvalidDevice);
+    Model &m = g_models[dev];
+    if (!m.P || m.path != path) {
+        std::vector<float> P;
+        SurNorm nrm;
+        int rc = load_model(path, P, nrm);
+        if (rc) return rc;
+        if (!m.P) {
+            cudaError_t e = cudaMalloc(&m.P, NPAR * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&m.Wf, (size_t)3 * SH * SH * 2);
+            if (e == cudaSuccess) e = cudaMalloc(&m.Wt, (size_t)3 * SH * SH * 2);
+            if (e != cudaSuccess) return cerr(e);
+        }
+        cudaError_t e = cudaMemcpyAsync(m.P, P.data(), NPAR * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cerr(e);
+        refresh_bf16_kernel<<<nblk(3 * SH * SH, 256), 256, 0, st>>>(m.P, m.Wf, m.Wt);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cerr(e);
+        m.path = path;
+        m.nrm = nrm;
+    }
+    *out = &m;
+    return TW_OK;
+}
+
+// MLP forward over `rows` (a multiple of 128) standardised-on-the-fly inputs:
+// H1 = layer 1 (CUDA cores), then the three hidden layers on the tensor cores
+// ping-ponging between HA and HB; returns the buffer holding layer 4.
+static int mlp_forward(const Model &m, int64_t rows, const float *X, __nv_bfloat16 *HA, __nv_bfloat16 *HB,
+                       __nv_bfloat16 *H1keep, __nv_bfloat16 **H2keep, float *XS, int *err, cudaStream_t st,
+                       __nv_bfloat16 **outH4) {
+    __nv_bfloat16 *h1 = H1keep ? H1keep : HA;
+    sur_layer1_kernel<<<nblk(rows * SH, 256), 256, 0, st>>>(rows, X, m.P, m.nrm, h1, XS);
+    __nv_bfloat16 *in = h1;
+    for (int l = 0; l < 3; l++) {
+        __nv_bfloat16 *out = H2keep ? H2keep[l] : ((in == HA) ? HB : HA);
+        GemmArgs g;
+        g.A = in;
+        g.B = m.Wf + (size_t)l * SH * SH;
+        g.M = (int)rows;
+        g.N = SH;
+        g.K = SH;
+        g.C = nullptr;
+        g.Cb = out;
+        g.bias = m.P + OBH[l];
+        g.relu = 1;
+        g.err = err;
+        cudaError_t e = gemm_bf16_tn(g, st);
+        if (e != cudaSuccess) return cerr(e);
+        in = out;
+    }
+    *outH4 = in;
+    return cerr(cudaGetLastError());
+}
+
+static bool dev_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace tw
+
+using namespace tw;
+
+extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, uint64_t seed, int epochs,
+                                  double *stats, const tw_opts *opts) {
+    if (!weights_path || nsamples < 4096 || nsamples > (int64_t)1 << 30 || epochs < 1 || epochs > 1000)
+        return TW_EINVAL;
+    tw_opts o;
+    tw_opts_default(&o);
+    if (opts) o = *opts;
+    std::lock_guard<std::mutex> lk(g_sm);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    const int64_t n = nsamples;
+    DevBufs B;
+    double *S, *Q, *RHO, *Y1, *Y2, *MUPS, *MU;
+    float *X, *T, *WT;
+    uint8_t *FLAG;
+    int32_t *LIST;
+    unsigned long long *NL;
+    int *err;
+    int rc = 0;
+    if ((rc = B.get(&S, n)) || (rc = B.get(&Q, n)) || (rc = B.get(&RHO, n)) || (rc = B.get(&Y1, n)) ||
+        (rc = B.get(&Y2, n)) || (rc = B.get(&MUPS, n)) || (rc = B.get(&MU, n)) || (rc = B.get(&X, n * SXP)) ||
+        (rc = B.get(&T, n)) || (rc = B.get(&WT, n)) || (rc = B.get(&FLAG, n)) || (rc = B.get(&LIST, n)) ||
+        (rc = B.get(&NL, 1)) || (rc = B.get(&err, 1)))
+        return rc;
+    // positions near caustics, point-source values and flags, contour labels
+    sur_sample_kernel<<<nblk(n, 128), 128, 0, st>>>(seed, n, S, Q, RHO, Y1, Y2);
+    sur_features_kernel<<<nblk(n, 128), 128, 0, st>>>(n, S, Q, RHO, Y1, Y2, X, MUPS, FLAG);
+    cudaMemsetAsync(NL, 0, 8, st);
+    cudaMemsetAsync(err, 0, 4, st);
+    compact_unflagged_kernel<<<nblk(n, 256), 256, 0, st>>>(n, FLAG, LIST, NL);
+    unsigned long long nl = 0;
+    cudaError_t e = cudaMemcpyAsync(&nl, NL, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cerr(e);
+    if (nl < 4096) return TW_EINVAL;  // not enough trainable samples
+    // labels one decade tighter than the 1e-4 target, in FP64 mode
+    rc = contour_positions(S, Q, RHO, Y1, Y2, LIST, (int64_t)nl, 1e-5, TW_PREC_FP64, 4096, MU, nullptr, st);
+    if (rc) return rc;
+    sur_targets_kernel<<<nblk(n, 256), 256, 0, st>>>(n, MU, MUPS, FLAG, T, WT);
+    // dense training set of the unflagged samples
+    const int BATCH = 4096;
+    const int64_t m = ((int64_t)nl / BATCH) * BATCH;
+    float *Xc, *Tc, *WTc;
+    if ((rc = B.get(&Xc, m * SXP)) || (rc = B.get(&Tc, m)) || (rc = B.get(&WTc, m))) return rc;
+    gather_train_kernel<<<nblk(m, 256), 256, 0, st>>>(m, LIST, X, T, WT, Xc, Tc, WTc);
+    // standardisation from up to 65536 training rows
+    const int64_t ns = m < 65536 ? m : 65536;
+    std::vector<float> hx(ns * SXP), ht(ns), hw(ns);
+    e = cudaMemcpyAsync(hx.data(), Xc, ns * SXP * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ht.data(), Tc, ns * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hw.data(), WTc, ns * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cerr(e);
+    SurNorm nrm;
+    double tsum = 0, tsq = 0, wsum = 0;
+    for (int k = 0; k < SNIN; k++) {
+        double a = 0, b = 0;
+        for (int64_t i = 0; i < ns; i++) { a += hx[i * SXP + k]; b += (double)hx[i * SXP + k] * hx[i * SXP + k]; }
+        a /= ns;
+        b = b / ns - a * a;
+        nrm.mean[k] = (float)a;
+        nrm.inv_std[k] = (float)(1.0 / sqrt(b > 1e-20 ? b : 1e-20));
+    }
+    for (int64_t i = 0; i < ns; i++) { tsum += hw[i] * ht[i]; tsq += hw[i] * ht[i] * ht[i]; wsum += hw[i]; }
+    const double tmean = tsum / (wsum > 0 ? wsum : 1), tstd = sqrt(fmax(tsq / (wsum > 0 ? wsum : 1) - tmean * tmean, 1e-20));
+    // initial weights (He-uniform, seeded), head bias at the target mean / spread
+    std::vector<float> hP(NPAR, 0.f);
+    uint64_t rs = seed ^ 0xA0761D6478BD642Full;
+    auto urand = [&]() {
+        rs += 0x9E3779B97F4A7C15ull;
+        uint64_t z = rs;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int i = 0; i < SH * SNIN; i++) hP[OW1 + i] = (float)((2 * urand() - 1) * sqrt(6.0 / SNIN));
+    for (int l = 0; l < 3; l++)
+        for (int i = 0; i < SH * SH; i++) hP[OWH[l] + i] = (float)((2 * urand() - 1) * sqrt(6.0 / SH));
+    for (int i = 0; i < 2 * SH; i++) hP[OW5 + i] = (float)((2 * urand() - 1) * 1e-3);
+    hP[OB5] = (float)tmean;
+    hP[OB5 + 1] = (float)log(tstd);
+    Model tm;
+    float *G, *M1, *M2, *LOSS;
+    __nv_bfloat16 *H[4], *GA, *GB2, *TA, *TB;
+    float *DOUT, *DH, *XS;
+    if ((rc = B.get(&tm.P, NPAR)) || (rc = B.get(&tm.Wf, 3 * SH * SH)) || (rc = B.get(&tm.Wt, 3 * SH * SH)) ||
+        (rc = B.get(&G, NPAR)) || (rc = B.get(&M1, NPAR)) || (rc = B.get(&M2, NPAR)) || (rc = B.get(&LOSS, 1)))
+        return rc;
+    for (int l = 0; l < 4; l++)
+        if ((rc = B.get(&H[l], (size_t)BATCH * SH))) return rc;
+    if ((rc = B.get(&GA, (size_t)BATCH * SH)) || (rc = B.get(&GB2, (size_t)BATCH * SH)) ||
+        (rc = B.get(&TA, (size_t)BATCH * SH)) || (rc = B.get(&TB, (size_t)BATCH * SH)) ||
+        (rc = B.get(&DOUT, 2 * BATCH)) || (rc = B.get(&DH, (size_t)BATCH * SH)) || (rc = B.get(&XS, (size_t)BATCH * SXP)))
+        return rc;
+    tm.nrm = nrm;
+    e = cudaMemcpyAsync(tm.P, hP.data(), NPAR * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M1, 0, NPAR * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M2, 0, NPAR * 4, st);
+    if (e != cudaSuccess) return cerr(e);
+    refresh_bf16_kernel<<<nblk(3 * SH * SH, 256), 256, 0, st>>>(tm.P, tm.Wf, tm.Wt);
+    const int64_t steps_per_epoch = m / BATCH;
+    const int64_t total = steps_per_epoch * epochs;
+    const float lr0 = 1e-3f, b1 = 0.9f, b2 = 0.999f;
+    double loss_sum = 0;
+    int loss_n = 0;
+    for (int64_t stp = 0; stp < total; stp++) {
+        const int64_t off = (stp % steps_per_epoch) * BATCH;
+        const float *Xb = Xc + off * SXP, *Tb = Tc + off, *Wb = WTc + off;
+        __nv_bfloat16 *hk[3] = {H[1], H[2], H[3]};
+        __nv_bfloat16 *h4 = nullptr;
+        if ((rc = mlp_forward(tm, BATCH, Xb, nullptr, nullptr, H[0], hk, XS, err, st, &h4))) return rc;
+        const bool last_epoch = stp >= total - steps_per_epoch;
+        cudaMemsetAsync(LOSS, 0, 4, st);
+        sur_head_train_kernel<<<nblk((int64_t)BATCH * 32, 256), 256, 0, st>>>(BATCH, H[3], tm.P, Tb, Wb, DOUT, GA,
+                                                                            LOSS);
+        sur_head_wgrad_kernel<<<nblk(2 * SH + 2, 256), 256, 0, st>>>(BATCH, DOUT, H[3], G);
+        // hidden layers, last to first: g (bf16, masked) of layer l+1 is in GA
+        for (int l = 2; l >= 0; l--) {
+            __nv_bfloat16 *hin = H[l];  // input of hidden GEMM l (H1, H2, H3)
+            dim3 tb(32, 8);
+            transpose_bf16_kernel<<<dim3(SH / 32, BATCH / 32), tb, 0, st>>>(BATCH, SH, GA, TA);   // g^T [SH][B]
+            transpose_bf16_kernel<<<dim3(SH / 32, BATCH / 32), tb, 0, st>>>(BATCH, SH, hin, TB);  // h^T [SH][B]
+            GemmArgs gw;
+            gw.A = TA; gw.B = TB; gw.M = SH; gw.N = SH; gw.K = BATCH;
+            gw.C = G + OWH[l]; gw.Cb = nullptr; gw.bias = nullptr; gw.relu = 0; gw.err = err;
+            if ((e = gemm_bf16_tn(gw, st)) != cudaSuccess) return cerr(e);
+            colsum_bf16_kernel<<<1, SH, 0, st>>>(BATCH, GA, G + OBH[l]);
+            GemmArgs gx;  // dh_in = g . W  (W^T stored [in][out] is the K-major B operand)
+            gx.A = GA; gx.B = tm.Wt + (size_t)l * SH * SH; gx.M = BATCH; gx.N = SH; gx.K = SH;
+            gx.C = DH; gx.Cb = nullptr; gx.bias = nullptr; gx.relu = 0; gx.err = err;
+            if ((e = gemm_bf16_tn(gx, st)) != cudaSuccess) return cerr(e);
+            if (l > 0) relu_mask_kernel<<<nblk((int64_t)BATCH * SH, 256), 256, 0, st>>>((int64_t)BATCH * SH, DH, hin, GB2);
+            __nv_bfloat16 *tmp = GA; GA = GB2; GB2 = tmp;
+        }
+        sur_layer1_bwd_kernel<<<1, SH, 0, st>>>(BATCH, DH, H[0], XS, G);
+        const double frac = (double)stp / (double)total;
+        const float lr = (float)(lr0 * (0.05 + 0.95 * 0.5 * (1.0 + cos(3.141592653589793 * frac))));
+        const float c1 = 1.f / (1.f - powf(b1, (float)(stp + 1))), c2 = 1.f / (1.f - powf(b2, (float)(stp + 1)));
+        adam_kernel<<<nblk(NPAR, 256), 256, 0, st>>>(NPAR, tm.P, G, M1, M2, lr, b1, b2, c1, c2);
+        refresh_bf16_kernel<<<nblk(3 * SH * SH, 256), 256, 0, st>>>(tm.P, tm.Wf, tm.Wt);
+        if (last_epoch) {
+            float l = 0;
+            if ((e = cudaMemcpyAsync(&l, LOSS, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cerr(e);
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cerr(e);
+            loss_sum += l;
+            loss_n++;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return cerr(e);
+    }
+    int herr = 0;
+    e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hP.data(), tm.P, NPAR * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cerr(e);
+    if (herr) return TW_ETIMEOUT;
+    if ((rc = save_model(weights_path, hP, nrm))) return rc;
+    {  // a model cached from an earlier file of the same name is stale now
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) g_models[dev].path.clear();
+    }
+    if (stats) {
+        stats[0] = (double)n;                       // positions drawn
+        stats[1] = (double)nl;                      // unflagged (labelled) positions
+        stats[2] = (double)m;                       // training rows used
+        stats[3] = loss_n ? loss_sum / loss_n : 0;  // mean NLL over the last epoch
+        stats[4] = tstd;                            // spread of the targets
+    }
+    return TW_OK;
+}
+
+extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const double *q, const double *rho,
+                                const double *y1, const double *y2, int64_t n, double rel_tol, double kappa,
+                                double *out, int64_t *n_fallback, const tw_opts *opts) {
+    if (!weights_path || n < 0 || !(rel_tol > 0) || !(kappa > 0) || !isfinite(rel_tol)) return TW_EINVAL;
+    if (n == 0) { if (n_fallback) *n_fallback = 0; return TW_OK; }
+    if (!s || !q || !rho || !y1 || !y2 || !out) return TW_EINVAL;
+    tw_opts o;
+    tw_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != TW_PREC_FP64 && o.precision != TW_PREC_MIXED) return TW_EINVAL;
+    std::lock_guard<std::mutex> lk(g_sm);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    const bool dev = dev_ptr(out);
+    const double *in[5] = {s, q, rho, y1, y2};
+    for (int k = 0; k < 5; k++)
+        if (dev_ptr(in[k]) != dev) return TW_EINVAL;
+    Model *m = nullptr;
+    int rc = model_for(weights_path, st, &m);
+    if (rc) return rc;
+    DevBufs B;
+    const double *din[5];
+    double *dout = out;
+    cudaError_t e;
+    if (!dev) {  // host arrays: stage through device memory
+        for (int k = 0; k < 5; k++) {
+            double *d;
+            if ((rc = B.get(&d, n))) return rc;
+            if ((e = cudaMemcpyAsync(d, in[k], n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cerr(e);
+            din[k] = d;
+        }
+        if ((rc = B.get(&dout, n))) return rc;
+    } else {
+        for (int k = 0; k < 5; k++) din[k] = in[k];
+    }
+    const int64_t CH = 1 << 20;
+    const int64_t chunk = n < CH ? ((n + 127) / 128) * 128 : CH;
+    float *X;
+    double *MUPS;
+    uint8_t *FLAG;
+    int32_t *LIST;
+    unsigned long long *NL;
+    int *err;
+    __nv_bfloat16 *HA, *HB;
+    if ((rc = B.get(&X, chunk * SXP)) || (rc = B.get(&MUPS, n)) || (rc = B.get(&FLAG, n)) || (rc = B.get(&LIST, n)) ||
+        (rc = B.get(&NL, 1)) || (rc = B.get(&err, 1)) || (rc = B.get(&HA, chunk * SH)) || (rc = B.get(&HB, chunk * SH)))
+        return rc;
+    cudaMemsetAsync(NL, 0, 8, st);
+    cudaMemsetAsync(err, 0, 4, st);
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
+        const int64_t rows = ((cn + 127) / 128) * 128;
+        if (rows > cn) cudaMemsetAsync(X + cn * SXP, 0, (rows - cn) * SXP * 4, st);
+        sur_features_kernel<<<nblk(cn, 128), 128, 0, st>>>(cn, din[0] + c0, din[1] + c0, din[2] + c0, din[3] + c0,
+                                                           din[4] + c0, X, MUPS + c0, FLAG + c0);
+        __nv_bfloat16 *h4 = nullptr;
+        if ((rc = mlp_forward(*m, rows, X, HA, HB, nullptr, nullptr, nullptr, err, st, &h4))) return rc;
+        sur_head_infer_kernel<<<nblk(cn * 32, 256), 256, 0, st>>>(cn, c0, h4, m->P, MUPS, FLAG, rel_tol,
+                                                                 (float)kappa, dout, LIST, NL);
+    }
+    unsigned long long nl = 0;
+    int herr = 0;
+    e = cudaMemcpyAsync(&nl, NL, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cerr(e);
+    if (herr) return TW_ETIMEOUT;
+    // contour-integration fallback: one persistent launch over the list
+    rc = contour_positions(din[0], din[1], din[2], din[3], din[4], LIST, (int64_t)nl, rel_tol, o.precision,
+                           o.max_samples, dout, nullptr, st);
+    if (rc) return rc;
+    if (!dev) {
+        if ((e = cudaMemcpyAsync(out, dout, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cerr(e);
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cerr(e);
+    if (n_fallback) *n_fallback = (int64_t)nl;
+    return TW_OK;
+}
+
+extern "C" int tw_surrogate_sample(uint64_t seed, int64_t n, double *s, double *q, double *rho, double *y1,
+                                   double *y2, void *stream) {
+    if (n < 0) return TW_EINVAL;
+    if (n == 0) return TW_OK;
+    if (!dev_ptr(s) || !dev_ptr(q) || !dev_ptr(rho) || !dev_ptr(y1) || !dev_ptr(y2)) return TW_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    sur_sample_kernel<<<nblk(n, 128), 128, 0, st>>>(seed, n, s, q, rho, y1, y2);
+    return cerr(cudaGetLastError());
+}

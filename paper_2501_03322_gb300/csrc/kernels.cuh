@@ -29,7 +29,8 @@ constexpr int WPB = TPB / 32;
 
 // Where the positions of a launch come from.
 struct WorkSrc {
-    int kind;  // 0: one lens, arrays of positions; 1: one light curve; 2: batch of light curves
+    int kind;  // 0: one lens, arrays of positions; 1: one light curve; 2: batch of light curves;
+               // 3: per-position lens (surrogate fallback and training labels)
     int64_t n;
     double s, q, rho;                      // kinds 0 and 1
     const double *y1, *y2;                 // kind 0
@@ -40,6 +41,9 @@ struct WorkSrc {
     int64_t ncurve;
     int64_t stride;                        // work item i is input position i * stride (calibration
                                            // sub-samples use stride > 1; outputs stay compact)
+    const double *ps, *pq, *prho;          // kind 3: per-position lens and source radius, with y1, y2
+    const int32_t *list;                   // kind 3: optional list of positions; work item i is
+                                           // position list[i] and its outputs go to index list[i]
 };
 
 struct KParams {
@@ -80,6 +84,11 @@ __device__ __forceinline__ bool fetch_position(const WorkSrc &w, int64_t idx, Po
     } else if (w.kind == 1) {
         P.s = w.s; P.q = w.q; P.rho = w.rho;
         trajectory(w.u0, w.alpha, w.t0, w.tE, w.times[idx], P.y1, P.y2);
+    } else if (w.kind == 3) {
+        const int64_t j = w.list ? (int64_t)w.list[idx] : idx;
+        P.s = w.ps[j]; P.q = w.pq[j]; P.rho = w.prho[j];
+        P.y1 = w.y1[j];
+        P.y2 = w.y2[j];
     } else {
         // curve k with offsets[k] <= idx < offsets[k+1]
         int64_t lo = 0, hi = w.ncurve - 1;
@@ -146,10 +155,11 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParam
             if (!isfinite(mu)) { status |= PS_NONFINITE; mu = __longlong_as_double(0x7ff8000000000000ll); }
         }
         if (lane == 0) {
-            kp.out[idx] = mu;
-            if (kp.err) kp.err[idx] = err;
-            if (kp.nsamp) kp.nsamp[idx] = nsamp;
-            if (kp.pstat) kp.pstat[idx] = (int8_t)status;
+            const unsigned long long o = (kp.src.kind == 3 && kp.src.list) ? (unsigned long long)kp.src.list[idx] : idx;
+            kp.out[o] = mu;
+            if (kp.err) kp.err[o] = err;
+            if (kp.nsamp) kp.nsamp[o] = nsamp;
+            if (kp.pstat) kp.pstat[o] = (int8_t)status;
         }
         idx++;
     }
@@ -171,6 +181,14 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParam
     cudaError_t occupancy_contour_##PREC##_##SPL(int *occ);
 
 cudaError_t launch_rcp_selftest(unsigned long long *max_err_bits, int n, cudaStream_t st);
+
+// Host (twinkle.cu): contour integration of n positions with per-position lens
+// and source radius (kind 3), device pointers, serialised with the library's
+// other launches.  With `list`, work item i is position list[i] and writes
+// out[list[i]] (and status[list[i]]).  Returns a TW_* code.
+int contour_positions(const double *s, const double *q, const double *rho, const double *y1, const double *y2,
+                      const int32_t *list, int64_t n, double tol, int prec, int max_samples, double *out,
+                      int8_t *status, cudaStream_t st);
 
 TW_DECLARE_LAUNCHER(0, 1)
 TW_DECLARE_LAUNCHER(0, 2)

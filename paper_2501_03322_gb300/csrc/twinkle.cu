@@ -367,6 +367,29 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     return warn;
 }
 
+int contour_positions(const double *s, const double *q, const double *rho, const double *y1, const double *y2,
+                      const int32_t *list, int64_t n, double tol, int prec, int max_samples, double *out,
+                      int8_t *status, cudaStream_t st) {
+    if (n == 0) return TW_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState *dp = nullptr;
+    int rc = dev_state(&dp);
+    if (rc) return rc;
+    WorkSrc w;
+    memset(&w, 0, sizeof(w));
+    w.kind = 3;
+    w.n = n;
+    w.stride = 1;
+    w.ps = s;
+    w.pq = q;
+    w.prho = rho;
+    w.y1 = y1;
+    w.y2 = y2;
+    w.list = list;
+    const LaunchCfg cfg = {2, 0, 1};
+    return launch(*dp, w, tol, prec, max_samples, cfg, false, out, nullptr, nullptr, status, st);
+}
+
 }  // namespace tw
 
 using namespace tw;

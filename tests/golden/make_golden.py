@@ -12,6 +12,7 @@ Files (text, one position per line: inputs, mu, oracle status):
   stress_resonant.txt     200 sampled positions of the resonant large-source set
   batch_lightcurves.txt   192 sampled (curve, time) points of the 4096-curve batch
   paper_worked.txt        the paper's worked configurations (Fig. 1, 2, 5)
+  surrogate_queries.txt   192 positions near the caustics of 8 lenses of the surrogate's range
 """
 from __future__ import annotations
 
@@ -131,7 +132,43 @@ def paper_worked():
     print("wrote", path, len(out), "rows")
 
 
-ALL = {"lightcurve_central": lightcurve_central, "map_planetary": map_planetary, "stress_resonant": stress_resonant,
+def surrogate_queries():
+    """Query positions near caustics for the surrogate path: 8 lenses with
+    log10 s ~ U[-0.5, 0.5], log10 q ~ U[-5, -1], log10 rho ~ U[-4, -2]; for
+    each, 24 positions = a random point of a random branch of the oracle's
+    caustic + a displacement uniform in a disc of 3x that branch's size."""
+    rng = np.random.default_rng(404)
+    rows = []
+    jobs = []
+    for k in range(8):
+        s = 10 ** rng.uniform(-0.5, 0.5)
+        q = 10 ** rng.uniform(-5, -1)
+        rho = 10 ** rng.uniform(-4, -2)
+        _, cc = O.caustic(s, q, 256)
+        pts = []
+        for _ in range(24):
+            b = rng.integers(4)
+            c = cc[rng.integers(256), b]
+            w = max(np.ptp(cc[:, b].real), np.ptp(cc[:, b].imag))
+            r = 3 * w * np.sqrt(rng.uniform())
+            a = rng.uniform(0, 2 * np.pi)
+            pts.append((c.real + r * np.cos(a), c.imag + r * np.sin(a)))
+        jobs.append((s, q, rho, np.array(pts)))
+
+    def run(job):
+        s, q, rho, pts = job
+        mu, st, nx = O.mag(s, q, rho, pts[:, 0], pts[:, 1], scan_K=256, nthreads=1)
+        return [(s, q, rho, p[0], p[1], m, a, b) for p, m, a, b in zip(pts, mu, st, nx)]
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
+        for r in ex.map(run, jobs):
+            rows.extend(r)
+    hdr = ("Surrogate queries: 8 lenses (seed 404) x 24 positions near the oracle's caustic (random branch point +\n"
+           "displacement within 3x the branch size); oracle magnifications.")
+    _write("surrogate_queries.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
+
+
+ALL = {"lightcurve_central": lightcurve_central, "surrogate_queries": surrogate_queries, "map_planetary": map_planetary, "stress_resonant": stress_resonant,
        "batch_lightcurves": batch_lightcurves, "paper_worked": paper_worked}
 
 if __name__ == "__main__":
