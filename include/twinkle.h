@@ -110,6 +110,12 @@ int tw_mag(double s, double q, double rho, const double *y1, const double *y2, i
 int tw_mag_ex(double s, double q, double rho, const double *y1, const double *y2, int64_t n,
               double rel_tol, double *out, const tw_opts *opts);
 
+/* As tw_mag_ex, with a lens (s[i], q[i]) and source radius rho[i] of its own
+ * for every position (contiguous float64 arrays of n elements); positions
+ * with an invalid lens or radius give NaN and TW_POS_NONFINITE. */
+int tw_mag_multi(const double *s, const double *q, const double *rho, const double *y1, const double *y2, int64_t n,
+                 double rel_tol, double *out, const tw_opts *opts);
+
 /* Light curve: magnification at n times of a source moving on a straight
  * line (the paper leaves the convention open; this library uses, with
  * tau = (t - t0)/tE,  y1 = tau cos(alpha) - u0 sin(alpha),
@@ -148,9 +154,11 @@ int tw_mag_noalloc(double s, double q, double rho, const double *y1, const doubl
 
 /* MLP surrogate (not in the paper; a systems pattern of this library).  A
  * BF16 network 5 -> 256 -> 256 -> 256 -> 256 -> 2 maps (log10 s, log10 q,
- * log10 rho, y1, y2) to r = ln(mu / mu_ps) and l = ln(sigma), mu_ps being the
- * point-source magnification at the source centre (images of Eq. 6, parity
- * and Jacobian of Eq. 7); the hidden layers run on the tensor cores.
+ * log10 rho, y1, y2) to r = ln(mu / A_hex) and l = ln(sigma), A_hex being the
+ * hexadecapole approximation of the finite-source magnification from
+ * point-source magnifications (images of Eq. 6, Jacobian of Eq. 7) at the
+ * source centre and at 8 points on rings of radius rho/2, rho and 2 rho; the hidden
+ * layers run on the tensor cores.
  *
  * tw_surrogate_train draws nsamples positions near caustics (a random point of
  * a random branch of the caustic of a random lens with log10 s ~ U[-0.5, 0.5],
@@ -165,15 +173,22 @@ int tw_surrogate_train(const char *weights_path, int64_t nsamples, uint64_t seed
                        const tw_opts *opts);
 
 /* Surrogate magnification of n queries with per-query lens and source radius
- * (arrays s, q, rho, y1, y2; host or device, all of one kind).  A query falls
- * back to contour integration (one persistent launch over the fallbacks, with
- * opts->precision and opts->max_samples) when it is flagged as near a caustic
- * (the image count differs between the centre and any of 8 points 2 rho away,
- * or min |J| < 0.1 at the centre) or when kappa * sigma > rel_tol.  out[i]
- * receives mu; *n_fallback (optional) the number of fallbacks.  Synchronous. */
+ * (arrays s, q, rho, y1, y2; host or device, all of one kind).  A query that
+ * is not flagged as near a caustic (the caustic, swept at 64 angles, comes
+ * within 4 rho of the centre; the image count differs between the centre and
+ * a ring point; min |J| < 0.1 at the centre; or the expansion's error
+ * estimate, the gap between its values from the rings (rho/2, rho) and
+ * (rho, 2 rho), exceeds 5% of the value) is answered without contour
+ * integration when its predicted error is within rel_tol: the expansion's
+ * error estimate is below 0.5 rel_tol (mu = A_hex), or the network's
+ * kappa * sigma <= rel_tol (mu = A_hex exp(r)).  All other queries fall back
+ * to contour integration (one persistent launch over them, with
+ * opts->precision and opts->max_samples).  out[i] receives mu; counts
+ * (optional, [3]) the number of fallbacks, of queries accepted by the
+ * network, and of queries accepted by the expansion.  Synchronous. */
 int tw_surrogate_mag(const char *weights_path, const double *s, const double *q, const double *rho,
                      const double *y1, const double *y2, int64_t n, double rel_tol, double kappa, double *out,
-                     int64_t *n_fallback, const tw_opts *opts);
+                     int64_t *counts, const tw_opts *opts);
 
 /* The training-position sampler of tw_surrogate_train, on its own: n seeded
  * positions near caustics into device arrays (asynchronous on `stream`). */
@@ -201,6 +216,14 @@ int tw_version(void);
  * These are the units of the FLOP accounting of the roofline report; the
  * paper has no counterpart (it reports no operation counts). */
 int tw_last_launch_work(int64_t out[5]);
+
+/* Device time, in milliseconds, of the most recent contour-integration kernel
+ * launch on the current device (every entry point above that integrates
+ * contours, including the fallback launch of tw_surrogate_mag), measured by
+ * two CUDA events recorded on the launch's stream directly before and after
+ * the kernel; waits for it.  TW_EINVAL if no launch has been timed.  No
+ * counterpart in the paper (a measurement hook of this library). */
+int tw_last_launch_ms(float *ms);
 
 /* Device self-test of the library's FP64 reciprocal (the hardware
  * approximation refined by two Newton-Raphson steps, used for every complex

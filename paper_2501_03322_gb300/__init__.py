@@ -77,6 +77,8 @@ def lib():
             L.tw_lightcurve.restype = I
             L.tw_lightcurve_ex.argtypes = [d, d, d, d, d, d, d, P, i64, d, P, P]
             L.tw_lightcurve_ex.restype = I
+            L.tw_mag_multi.argtypes = [P, P, P, P, P, i64, d, P, P]
+            L.tw_mag_multi.restype = I
             L.tw_lightcurve_batch.argtypes = [P, P, P, i64, d, P, P]
             L.tw_lightcurve_batch.restype = I
             L.tw_status_str.argtypes = [I]
@@ -85,6 +87,8 @@ def lib():
             L.tw_version.restype = I
             L.tw_last_launch_work.argtypes = [P]
             L.tw_last_launch_work.restype = I
+            L.tw_last_launch_ms.argtypes = [P]
+            L.tw_last_launch_ms.restype = I
             L.tw_selftest.argtypes = [P]
             L.tw_selftest.restype = I
             L.tw_mag_noalloc.argtypes = [d, d, d, P, P, i64, d, P, I, I, P]
@@ -176,6 +180,13 @@ def last_launch_work() -> dict:
     return dict(samples=int(a[0]), sweeps64=int(a[1]), sweeps32=int(a[2]), edges=int(a[3]), newton64=int(a[4]))
 
 
+def last_launch_ms() -> float:
+    """Device time (ms) of the last contour-integration kernel launch, from CUDA events on its stream."""
+    a = np.zeros(1, np.float32)
+    _check(lib().tw_last_launch_ms(a.ctypes.data_as(ctypes.c_void_p)))
+    return float(a[0])
+
+
 def gemm_bf16(A, B, out=None, stream=None):
     """C = A @ B.T on the tensor cores (tw_gemm_bf16); A [M, K], B [N, K] bf16 CUDA tensors."""
     import torch
@@ -209,17 +220,22 @@ def surrogate_sample(seed, n, device="cuda"):
 
 
 def surrogate_mag(path, s, q, rho, y1, y2, rel_tol=1e-4, kappa=3.0, precision=PREC_FP64, max_samples=4096, out=None,
-                  stream=None):
-    """Surrogate magnification with contour fallback (tw_surrogate_mag); returns (out, n_fallback)."""
+                  stream=None, details=False):
+    """Surrogate magnification with contour fallback (tw_surrogate_mag).
+
+    Returns (out, n_fallback) or, with details=True, (out, counts) where counts =
+    dict(fallback=..., network=..., expansion=...)."""
     arrs = [_prep(a) for a in (s, q, rho, y1, y2)]
     n = int(arrs[0].shape[0])
     if out is None:
         out = _alloc_like(arrs[0], n, np.float64, "float64")
-    nf = ctypes.c_int64(0)
+    c = np.zeros(3, np.int64)
     o = make_opts(precision, 64, max_samples, _stream_of(arrs[0], stream))
     _check(lib().tw_surrogate_mag(str(path).encode(), *[_ptr(a) for a in arrs], n, rel_tol, kappa, _ptr(out),
-                                  ctypes.byref(nf), ctypes.byref(o)))
-    return out, int(nf.value)
+                                  c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o)))
+    if details:
+        return out, dict(fallback=int(c[0]), network=int(c[1]), expansion=int(c[2]))
+    return out, int(c[0])
 
 
 def selftest_rcp() -> float:
@@ -263,6 +279,24 @@ def mag_noalloc(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, max_sample
     _check(lib().tw_mag_noalloc(s, q, rho, _ptr(y1), _ptr(y2), n, rel_tol, _ptr(out), int(precision),
                                 int(max_samples), st))
     return out
+
+
+def mag_multi(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64, max_samples=4096,
+              out=None, details=False, stream=None, autotune=False, use_graph=False):
+    """Magnification of positions each with its own lens and source radius (tw_mag_multi)."""
+    arrs = [_prep(a) for a in (s, q, rho, y1, y2)]
+    n = int(arrs[0].shape[0])
+    if out is None:
+        out = _alloc_like(arrs[0], n, np.float64, "float64")
+    err = nsamp = status = None
+    if details:
+        err = _alloc_like(arrs[0], n, np.float64, "float64")
+        nsamp = _alloc_like(arrs[0], n, np.int32, "int32")
+        status = _alloc_like(arrs[0], n, np.int8, "int8")
+    o = make_opts(precision, samples_per_iter, max_samples, _stream_of(arrs[0], stream), err, nsamp, status,
+                  autotune, use_graph)
+    _check(lib().tw_mag_multi(*[_ptr(a) for a in arrs], n, rel_tol, _ptr(out), ctypes.byref(o)))
+    return (out, err, nsamp, status) if details else out
 
 
 def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,

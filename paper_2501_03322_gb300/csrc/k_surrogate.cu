@@ -3,19 +3,25 @@
 //
 // The network maps x = (log10 s, log10 q, log10 rho, y1, y2) (standardised)
 // through 5 -> 256 -> 256 -> 256 -> 256 -> 2 (ReLU) to (r, l): r is the
-// logarithm of the ratio of the finite-source magnification to the
-// point-source magnification at the source centre, l = ln(sigma) its predicted
-// uncertainty, so mu = mu_ps exp(r).  Learning the finite-source correction on
-// top of the point-source value keeps the BF16 network's errors on a quantity
-// that is small away from caustics.  The three 256 x 256 layers run on the
+// logarithm of the ratio of the finite-source magnification to its
+// hexadecapole approximation A_hex (point-source magnifications at the centre
+// and on rings, Gould 2008; the paper tests point-source adequacy the same
+// way, Sec. 2.3), l = ln(sigma) its predicted uncertainty, so mu = A_hex exp(r).
+// Learning only what the expansion misses keeps the BF16 network's errors on
+// a quantity that is tiny away from caustics.  The three 256 x 256 layers run on the
 // tensor cores (k_gemm.cu, BF16 weights and activations, FP32 accumulation);
 // the 5 -> 256 input layer and the 256 -> 2 head run in FP32 on CUDA cores.
 //
-// Inference: per query, the point-source images at the centre (Eq. 6
-// quintic, FP32 Aberth + FP64 Newton, residual ghost test, mu_ps = sum 1/|J|),
-// a near-caustic flag (the image count differs between the centre and any of
-// 8 points at distance 2 rho, or min |J| < 0.1 at the centre), the MLP, and
-// the fallback decision: flagged, or kappa * sigma > rel_tol.  Fallback
+// Inference: per query, point-source images (Eq. 6 quintic, FP32 Aberth +
+// FP64 Newton, residual ghost test, A = sum 1/|J|) at the centre and at 8
+// points on each of three rings (radius rho/2, rho and 2 rho), the hexadecapole
+// approximation with its error estimate, a near-caustic flag (the image count
+// differs between the centre and a ring point, min |J| < 0.1 at the centre, or
+// the error estimate exceeds 5% of the value), the MLP, and the fallback
+// decision: flagged, or neither the expansion's error estimate nor
+// kappa * sigma is within rel_tol.  The flag also sweeps the
+// caustic itself: a caustic smaller than the ring spacing can sit inside the
+// source without any ring point seeing it.  Fallback
 // queries are integrated by the contour kernel in one persistent launch.
 //
 // Training: positions are drawn near caustics (a random point of a random
@@ -242,9 +248,84 @@ __device__ int point_images(const LensK &L, cxd y, cxd z[5], double &mu_ps, doub
     return count;
 }
 
+// Is the caustic within `reach` of the source centre y0 (secondary frame)?  The
+// critical curve (the sampler's quartic above) is swept at NCAU angles in FP32 with
+// warm-started Aberth iterations; each branch's caustic points form a
+// polyline, and the query is near when a segment comes within `reach` plus
+// the segment's length (slack for the arc the chord cuts off).
+constexpr int NCAU = 64;
+__device__ bool caustic_within(float s, float m2, float m1, cxf y0, float reach) {
+    cxf z[4];
+    const float r0 = 1.0f + s;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float sn, cs;
+        sincosf(1.5707963f * k + 0.3f, &sn, &cs);
+        z[k] = {-0.5f * s + r0 * cs, r0 * sn};
+    }
+    cxf prev[4];
+    bool near = false;
+    for (int k = 0; k < NCAU && !near; k++) {
+        float sn, cs;
+        sincosf(6.2831853f * k / NCAU, &sn, &cs);
+        const cxf e = {cs, sn};
+        cxf c[5];
+        c[4] = e;
+        c[3] = (2.0f * s) * e;
+        c[2] = {s * s * cs - 1.0f, s * s * sn};
+        c[1] = {-2.0f * s * m2, 0.0f};
+        c[0] = {-m2 * s * s, 0.0f};
+        for (int it = 0; it < (k == 0 ? 120 : 30); it++) {
+            cxf S4[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) S4[a] = {0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = a + 1; b < 4; b++) {
+                    const cxf r = inv(z[a] - z[b]);
+                    S4[a] = S4[a] + r;
+                    S4[b] = S4[b] - r;
+                }
+            float wmax = 0.f, zmax = 0.f;
+            cxf w[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                cxf p = c[4], d = {0.f, 0.f};
+#pragma unroll
+                for (int t = 3; t >= 0; t--) {
+                    d = d * z[a] + p;
+                    p = p * z[a] + c[t];
+                }
+                w[a] = cdiv(p, d - p * S4[a]);
+                wmax = fmaxf(wmax, norm2(w[a]));
+                zmax = fmaxf(zmax, norm2(z[a]));
+            }
+#pragma unroll
+            for (int a = 0; a < 4; a++) z[a] = z[a] - w[a];
+            if (wmax <= 1e-12f * (zmax + 1e-30f)) break;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const cxf g = m1 * inv(cxf{z[a].x + s, z[a].y}) + m2 * inv(z[a]);
+            const cxf cpt = z[a] - conj(g);  // caustic point
+            if (k > 0) {
+                const cxf d = cpt - prev[a], v = y0 - prev[a];
+                const float L2 = norm2(d);
+                const float t = L2 > 0.f ? fminf(fmaxf(dot(v, d) / L2, 0.f), 1.f) : 0.f;
+                const cxf cl = {prev[a].x + t * d.x - y0.x, prev[a].y + t * d.y - y0.y};
+                const float lim = reach + sqrtf(L2);
+                if (norm2(cl) < lim * lim) near = true;
+            }
+            prev[a] = cpt;
+        }
+    }
+    return near;
+}
+
 // Raw features, point-source magnification and near-caustic flag per query.
 __global__ void sur_features_kernel(int64_t n, const double *S, const double *Q, const double *RHO, const double *Y1,
-                                    const double *Y2, float *X, double *MUPS, uint8_t *FLAG) {
+                                    const double *Y2, float *X, double *MUPS, uint8_t *FLAG, float *HEXE) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = S[i], q = Q[i], rho = RHO[i], y1 = Y1[i], y2 = Y2[i];
@@ -257,7 +338,7 @@ __global__ void sur_features_kernel(int64_t n, const double *S, const double *Q,
     x[5] = x[6] = x[7] = 0.f;
     const bool ok = s > 0 && q > 0 && rho > 0 && isfinite(s) && isfinite(q) && isfinite(rho) && isfinite(y1) &&
                     isfinite(y2);
-    if (!ok) { MUPS[i] = __longlong_as_double(0x7ff8000000000000ll); FLAG[i] = 1; return; }
+    if (!ok) { MUPS[i] = __longlong_as_double(0x7ff8000000000000ll); FLAG[i] = 1; HEXE[i] = 1.f; return; }
     if (q > 1.0) { q = 1.0 / q; y1 = -y1; }  // mass-swap symmetry (see kernels.cuh)
     LensK L;
     L.s = s;
@@ -267,20 +348,52 @@ __global__ void sur_features_kernel(int64_t n, const double *S, const double *Q,
     const cxd y0 = {y1 - s * L.m1, y2};
     cxd z[5];
     initial_roots(s, y0, z);
-    double mu, minJ;
-    const int c0 = point_images<true>(L, y0, z, mu, minJ);
-    bool flag = !(isfinite(mu) && mu >= 1.0 - 1e-3) || minJ < 0.1;
-    // the image count at 8 points 2 rho away must equal the centre's
-    for (int k = 0; k < 8 && !flag; k++) {
-        double sn, cs;
-        sincos(0.7853981633974483 * k + 0.2, &sn, &cs);
-        const cxd yk = {y0.x + 2.0 * rho * cs, y0.y + 2.0 * rho * sn};
-        cxd zk[5] = {z[0], z[1], z[2], z[3], z[4]};
-        double m, mj;
-        if (point_images<false>(L, yk, zk, m, mj) != c0) flag = true;
+    double A0, minJ;
+    const int c0 = point_images<true>(L, y0, z, A0, minJ);
+    bool flag = !(isfinite(A0) && A0 >= 1.0 - 1e-3) || minJ < 0.1;
+    // within 4 rho (not just 2 rho): closer than that the ring at 2 rho nears
+    // the caustic and the expansion's error estimate is no longer reliable
+    if (!flag) flag = caustic_within((float)s, (float)L.m2, (float)L.m1, to_f(y0), (float)(4.0 * rho) + 1e-6f);
+    // Point-source magnifications averaged over 8 points on rings of radius
+    // rho/2, rho and 2 rho.  For a smooth A, the average over a ring of radius
+    // r is A0 + c1 r^2 + c2 r^4 + c3 r^6 + ... (c1 = lap A / 4, c2 = lap^2 A / 64)
+    // and the disc average is A0 + c1 rho^2/2 + c2 rho^4/3 + c3 rho^6/4 + ...
+    // Two rings at lam rho and 2 lam rho fix c1 and c2 (the hexadecapole
+    // approximation, Gould 2008, with rings of other radii); the c3 term they
+    // leave out shifts the result by -(7/12) c3 rho^6 for lam = 1 and by
+    // +(1/24) c3 rho^6 for lam = 1/2.  The lam = 1/2 value is returned and the
+    // difference of the two, 15/24 c3 rho^6 (about 15 times its error while
+    // the series converges), is its error estimate.  The image count must be
+    // the centre's at every ring point (otherwise a caustic is within 2 rho).
+    double R[3] = {0.0, 0.0, 0.0};
+    for (int ring = 0; ring < 3 && !flag; ring++)
+        for (int k = 0; k < 8 && !flag; k++) {
+            double sn, cs;
+            sincos(0.7853981633974483 * k + 0.2, &sn, &cs);
+            const double r = (0.5 * (1 << ring)) * rho;
+            const cxd yk = {y0.x + r * cs, y0.y + r * sn};
+            cxd zk[5] = {z[0], z[1], z[2], z[3], z[4]};
+            double m, mj;
+            if (point_images<true>(L, yk, zk, m, mj) != c0 || !isfinite(m)) flag = true;
+            R[ring] += 0.125 * m;
+        }
+    double Ahex = A0, hexe = 1.0;
+    if (!flag) {
+        // disc average from the rings at lam rho and 2 lam rho
+        auto disc = [A0](double Ra, double Rb, double lam) {
+            const double d1 = Ra - A0, d2 = Rb - A0, l2 = lam * lam;
+            const double c2 = (d2 - 4.0 * d1) / (12.0 * l2 * l2);  // c2 rho^4
+            const double c1 = d1 / l2 - c2 * l2;                   // c1 rho^2
+            return A0 + 0.5 * c1 + c2 / 3.0;
+        };
+        Ahex = disc(R[0], R[1], 0.5);
+        hexe = fabs(disc(R[1], R[2], 1.0) - Ahex) / Ahex;
+        // a series that is not converging marks the neighbourhood of a caustic
+        if (!(Ahex > 0.0) || !(hexe <= 0.05)) flag = true;
     }
-    MUPS[i] = mu;
+    MUPS[i] = Ahex;
     FLAG[i] = flag ? 1 : 0;
+    HEXE[i] = (float)fmin(hexe, 1.0);
 }
 
 // ------------------------------------------------------------- MLP kernels
@@ -303,8 +416,8 @@ __global__ void sur_layer1_kernel(int64_t rows, const float *X, const float *P, 
 
 // Head (256 -> 2) and fallback decision; one warp per query.
 __global__ void sur_head_infer_kernel(int64_t n, int64_t row0, const __nv_bfloat16 *H4, const float *P,
-                                      const double *MUPS, const uint8_t *FLAG, double tol, float kappa, double *OUT,
-                                      int32_t *LIST, unsigned long long *NLIST) {
+                                      const double *MUPS, const uint8_t *FLAG, const float *HEXE, double tol,
+                                      float kappa, double *OUT, int32_t *LIST, unsigned long long *NLIST) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n) return;
@@ -325,14 +438,18 @@ __global__ void sur_head_infer_kernel(int64_t n, int64_t row0, const __nv_bfloat
     if (lane == 0) {
         const int64_t g = row0 + w;
         const float r = a + P[OB5], l = b + P[OB5 + 1];
-        const double mu = MUPS[g] * exp((double)r);
-        const bool fb = FLAG[g] || !(kappa * expf(l) <= (float)tol) || !isfinite(mu);
-        if (fb) {
+        // accepted by the expansion itself when its error estimate is within
+        // half the tolerance, else by the network when kappa sigma <= tol
+        const bool hex_ok = HEXE[g] <= 0.5f * (float)tol;
+        const bool mlp_ok = kappa * expf(l) <= (float)tol;
+        const double mu = hex_ok ? MUPS[g] : MUPS[g] * exp((double)r);
+        if (FLAG[g] || !(hex_ok || mlp_ok) || !isfinite(mu)) {
             const unsigned long long slot = atomicAdd(NLIST, 1ull);
             LIST[slot] = (int32_t)g;
             OUT[g] = __longlong_as_double(0x7ff8000000000000ll);
         } else {
             OUT[g] = mu;
+            atomicAdd(NLIST + (hex_ok ? 2 : 1), 1ull);
         }
     }
 }
@@ -665,7 +782,9 @@ extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, ui
         return rc;
     // positions near caustics, point-source values and flags, contour labels
     sur_sample_kernel<<<nblk(n, 128), 128, 0, st>>>(seed, n, S, Q, RHO, Y1, Y2);
-    sur_features_kernel<<<nblk(n, 128), 128, 0, st>>>(n, S, Q, RHO, Y1, Y2, X, MUPS, FLAG);
+    float *HEXE;
+    if ((rc = B.get(&HEXE, n))) return rc;
+    sur_features_kernel<<<nblk(n, 128), 128, 0, st>>>(n, S, Q, RHO, Y1, Y2, X, MUPS, FLAG, HEXE);
     cudaMemsetAsync(NL, 0, 8, st);
     cudaMemsetAsync(err, 0, 4, st);
     compact_unflagged_kernel<<<nblk(n, 256), 256, 0, st>>>(n, FLAG, LIST, NL);
@@ -812,9 +931,9 @@ extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, ui
 
 extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const double *q, const double *rho,
                                 const double *y1, const double *y2, int64_t n, double rel_tol, double kappa,
-                                double *out, int64_t *n_fallback, const tw_opts *opts) {
+                                double *out, int64_t *counts, const tw_opts *opts) {
     if (!weights_path || n < 0 || !(rel_tol > 0) || !(kappa > 0) || !isfinite(rel_tol)) return TW_EINVAL;
-    if (n == 0) { if (n_fallback) *n_fallback = 0; return TW_OK; }
+    if (n == 0) { if (counts) counts[0] = counts[1] = counts[2] = 0; return TW_OK; }
     if (!s || !q || !rho || !y1 || !y2 || !out) return TW_EINVAL;
     tw_opts o;
     tw_opts_default(&o);
@@ -846,7 +965,7 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
     }
     const int64_t CH = 1 << 20;
     const int64_t chunk = n < CH ? ((n + 127) / 128) * 128 : CH;
-    float *X;
+    float *X, *HEXE;
     double *MUPS;
     uint8_t *FLAG;
     int32_t *LIST;
@@ -854,28 +973,30 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
     int *err;
     __nv_bfloat16 *HA, *HB;
     if ((rc = B.get(&X, chunk * SXP)) || (rc = B.get(&MUPS, n)) || (rc = B.get(&FLAG, n)) || (rc = B.get(&LIST, n)) ||
-        (rc = B.get(&NL, 1)) || (rc = B.get(&err, 1)) || (rc = B.get(&HA, chunk * SH)) || (rc = B.get(&HB, chunk * SH)))
+        (rc = B.get(&NL, 3)) || (rc = B.get(&err, 1)) || (rc = B.get(&HA, chunk * SH)) ||
+        (rc = B.get(&HB, chunk * SH)) || (rc = B.get(&HEXE, n)))
         return rc;
-    cudaMemsetAsync(NL, 0, 8, st);
+    cudaMemsetAsync(NL, 0, 24, st);
     cudaMemsetAsync(err, 0, 4, st);
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
         const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
         const int64_t rows = ((cn + 127) / 128) * 128;
         if (rows > cn) cudaMemsetAsync(X + cn * SXP, 0, (rows - cn) * SXP * 4, st);
         sur_features_kernel<<<nblk(cn, 128), 128, 0, st>>>(cn, din[0] + c0, din[1] + c0, din[2] + c0, din[3] + c0,
-                                                           din[4] + c0, X, MUPS + c0, FLAG + c0);
+                                                           din[4] + c0, X, MUPS + c0, FLAG + c0, HEXE + c0);
         __nv_bfloat16 *h4 = nullptr;
         if ((rc = mlp_forward(*m, rows, X, HA, HB, nullptr, nullptr, nullptr, err, st, &h4))) return rc;
-        sur_head_infer_kernel<<<nblk(cn * 32, 256), 256, 0, st>>>(cn, c0, h4, m->P, MUPS, FLAG, rel_tol,
+        sur_head_infer_kernel<<<nblk(cn * 32, 256), 256, 0, st>>>(cn, c0, h4, m->P, MUPS, FLAG, HEXE, rel_tol,
                                                                  (float)kappa, dout, LIST, NL);
     }
-    unsigned long long nl = 0;
+    unsigned long long cnt[3] = {0, 0, 0};
     int herr = 0;
-    e = cudaMemcpyAsync(&nl, NL, 8, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(cnt, NL, 24, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cerr(e);
     if (herr) return TW_ETIMEOUT;
+    const unsigned long long nl = cnt[0];
     // contour-integration fallback: one persistent launch over the list
     rc = contour_positions(din[0], din[1], din[2], din[3], din[4], LIST, (int64_t)nl, rel_tol, o.precision,
                            o.max_samples, dout, nullptr, st);
@@ -884,7 +1005,11 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
         if ((e = cudaMemcpyAsync(out, dout, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cerr(e);
     }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cerr(e);
-    if (n_fallback) *n_fallback = (int64_t)nl;
+    if (counts) {
+        counts[0] = (int64_t)cnt[0];
+        counts[1] = (int64_t)cnt[1];
+        counts[2] = (int64_t)cnt[2];
+    }
     return TW_OK;
 }
 

@@ -43,6 +43,8 @@ struct DevState {
     char *stage = nullptr;          // device staging for host-pointer calls
     size_t stage_bytes = 0;
     cudaEvent_t last = nullptr;     // completion of the previous launch (serialises calls)
+    cudaEvent_t t0 = nullptr, t1 = nullptr;  // timing events around the latest kernel launch
+    bool timed = false;             // t0/t1 hold a launch
     char *calib = nullptr;          // outputs of autotuning calibration runs
     size_t calib_bytes = 0;
     cudaGraphExec_t graph = nullptr;  // replayable {counter reset, persistent kernel}
@@ -67,6 +69,8 @@ static int dev_state(DevState **out) {
         if ((e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e);
         if ((e = cudaMalloc(&d.counter, 64)) != cudaSuccess) return cuda_fail(e);
         if ((e = cudaEventCreateWithFlags(&d.last, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaEventCreate(&d.t0)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaEventCreate(&d.t1)) != cudaSuccess) return cuda_fail(e);
         cudaDeviceProp prop;
         if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return cuda_fail(e);
         snprintf(d.name, sizeof(d.name), "%s", prop.name);
@@ -167,7 +171,11 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
                     if (!ok) { (void)cudaGetLastError(); cudaGraphExecDestroy(d.graph); d.graph = nullptr; }
                 }
                 if (!ok) ok = cudaGraphInstantiate(&d.graph, g, 0) == cudaSuccess;
-                if (ok && cudaGraphLaunch(d.graph, st) == cudaSuccess) graphed = true;
+                if (ok) {
+                    d.timed = cudaEventRecord(d.t0, st) == cudaSuccess;
+                    graphed = cudaGraphLaunch(d.graph, st) == cudaSuccess;
+                    d.timed = d.timed && graphed && cudaEventRecord(d.t1, st) == cudaSuccess;
+                }
             }
             if (g) cudaGraphDestroy(g);
         }
@@ -175,8 +183,11 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     }
     if (!graphed) {
         if ((e = cudaMemsetAsync(d.counter, 0, 6 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_fail(e);
-        if ((e = lf((unsigned)blocks, st, kp)) != cudaSuccess) return cuda_fail(e);
+        d.timed = cudaEventRecord(d.t0, st) == cudaSuccess;
+        if ((e = lf((unsigned)blocks, st, kp)) != cudaSuccess) { d.timed = false; return cuda_fail(e); }
+        d.timed = d.timed && cudaEventRecord(d.t1, st) == cudaSuccess;
     }
+    (void)cudaGetLastError();
     if ((e = cudaEventRecord(d.last, st)) != cudaSuccess) return cuda_fail(e);
     return TW_OK;
 }
@@ -291,8 +302,8 @@ static int autotune(DevState &d, const WorkSrc &src, double tol, int prec, int m
 // ins/insz: input arrays (host or device) and their byte sizes; the staged
 // device copies are handed to `bind`, which fills src from them.
 struct Call {
-    const void *in[4];
-    size_t insz[4];
+    const void *in[5];
+    size_t insz[5];
     int nin;
     int64_t n;  // positions (outputs)
 };
@@ -317,7 +328,7 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     if (o.err_out && is_device_ptr(o.err_out) != dev) return TW_EINVAL;
     if (o.nsamp_out && is_device_ptr(o.nsamp_out) != dev) return TW_EINVAL;
     if (o.pos_status && is_device_ptr(o.pos_status) != dev) return TW_EINVAL;
-    const void *din[4];
+    const void *din[5];
     LaunchCfg cfg = {o.samples_per_iter / 32, 0, 1};
     if (dev) {
         for (int i = 0; i < c.nin; i++) din[i] = c.in[i];
@@ -327,7 +338,7 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
                       o.pos_status, st);
     }
     // host pointers: stage inputs and outputs through device memory
-    size_t off[4], total = 0;
+    size_t off[5], total = 0;
     for (int i = 0; i < c.nin; i++) { off[i] = total; total += align256(c.insz[i]); }
     const size_t o_out = total; total += align256((size_t)c.n * 8);
     const size_t o_err = total; total += align256((size_t)c.n * 8);
@@ -454,6 +465,28 @@ int tw_lightcurve(double s, double q, double rho, double u0, double alpha, doubl
     return tw_lightcurve_ex(s, q, rho, u0, alpha, t0, tE, times, n, rel_tol, out, nullptr);
 }
 
+int tw_mag_multi(const double *s, const double *q, const double *rho, const double *y1, const double *y2, int64_t n,
+                 double rel_tol, double *out, const tw_opts *opts) {
+    if (n < 0 || !finite_pos(rel_tol)) return TW_EINVAL;
+    if (n > 0 && (!s || !q || !rho || !y1 || !y2 || !out)) return TW_EINVAL;
+    Call c;
+    c.nin = 5;
+    const double *a[5] = {s, q, rho, y1, y2};
+    for (int i = 0; i < 5; i++) { c.in[i] = a[i]; c.insz[i] = (size_t)n * 8; }
+    c.n = n;
+    return run_call(c, rel_tol, opts, out, [&](const void **din) {
+        WorkSrc w;
+        memset(&w, 0, sizeof(w));
+        w.kind = 3; w.n = n; w.stride = 1;
+        w.ps = (const double *)din[0];
+        w.pq = (const double *)din[1];
+        w.prho = (const double *)din[2];
+        w.y1 = (const double *)din[3];
+        w.y2 = (const double *)din[4];
+        return w;
+    });
+}
+
 int tw_lightcurve_batch(const double *params, const int64_t *offsets, const double *times, int64_t ncurve,
                         double rel_tol, double *out, const tw_opts *opts) {
     if (ncurve < 0 || !finite_pos(rel_tol)) return TW_EINVAL;
@@ -519,6 +552,19 @@ int tw_selftest(double *rcp_max_rel_err) {
     if (e == cudaSuccess) e = cudaMemcpy(&h, slot, 8, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e);
     memcpy(rcp_max_rel_err, &h, 8);
+    return TW_OK;
+}
+
+int tw_last_launch_ms(float *ms) {
+    if (!ms) return TW_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState *dp = nullptr;
+    int rc = dev_state(&dp);
+    if (rc) return rc;
+    if (!dp->timed) return TW_EINVAL;
+    cudaError_t e = cudaEventSynchronize(dp->t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, dp->t0, dp->t1);
+    if (e != cudaSuccess) return cuda_fail(e);
     return TW_OK;
 }
 

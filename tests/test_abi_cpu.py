@@ -70,6 +70,7 @@ def test_null_pointers_and_empty_calls():
     assert lib.tw_lightcurve(1.0, 1e-3, 1e-3, 0.1, 1.0, 0.0, 0.0, None, 0, 1e-4, None) == P.TW_EINVAL  # tE = 0
     assert lib.tw_lightcurve(1.0, 1e-3, 1e-3, 0.1, 1.0, 0.0, 20.0, None, 0, 1e-4, None) == P.TW_OK
     assert lib.tw_last_launch_work(None) == P.TW_EINVAL
+    assert lib.tw_last_launch_ms(None) == P.TW_EINVAL
 
 
 def test_batch_offsets_validated_on_host():

@@ -188,3 +188,14 @@ def test_autotuned_and_graph_replayed_batch(tmp_path, monkeypatch):
             ok = np.array([int(r[4]) == 0 for r in rows])
             assert rel_err(got[idx][ok], ref[ok]).max() <= TOL
     assert (tmp_path / "tune.txt").exists()
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_mag_multi_per_position_lens(prec):
+    """Per-position lenses (tw_mag_multi) on 192 oracle-placed positions near the
+    caustics of 8 random lenses of the surrogate's range."""
+    rows = load("surrogate_queries.txt")
+    a = np.array([[float(v) for v in r[:6]] for r in rows])
+    ok = np.array([int(r[6]) == 0 for r in rows])
+    mu = P.mag_multi(a[:, 0], a[:, 1], a[:, 2], a[:, 3], a[:, 4], rel_tol=TOL, precision=prec)
+    assert rel_err(mu[ok], a[ok, 5]).max() <= TOL
