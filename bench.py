@@ -97,7 +97,8 @@ def config_of(wl, mode, n_gpus):
 
 
 KERNEL_SOURCES = ("cx.cuh", "lens.cuh", "contour.cuh", "kernels.cuh", "k_fp64_spl1.cu", "k_fp64_spl2.cu",
-                  "k_fp64_spl4.cu", "k_mixed_spl1.cu", "k_mixed_spl2.cu", "k_mixed_spl4.cu")
+                  "k_fp64_spl4.cu", "k_mixed_spl1.cu", "k_mixed_spl2.cu", "k_mixed_spl4.cu", "k_fp64_repair.cu",
+                  "k_mixed_repair.cu")
 
 
 def sources_sha():
@@ -231,14 +232,16 @@ def launched_contour(wl):
 
 
 def gpu_launches(wl, steps):
-    """Kernels of this library launched in the timed steps: one contour launch
-    per step; a surrogate step launches, per chunk of 2^20 queries, the
-    feature, input-layer, three tensor-core GEMM and head kernels, then the
-    contour kernel over its fallbacks (when there are any)."""
+    """Kernels of this library launched in the timed steps: a contour
+    integration is two launches (the main pass and the slope-repair pass over
+    the positions it queued, usually none); a surrogate step launches, per
+    chunk of 2^20 queries, the feature, input-layer, three tensor-core GEMM and
+    head kernels, then contour integration of its fallbacks (when there are
+    any)."""
     if wl["kind"] != "surrogate":
-        return steps
+        return 2 * steps
     chunks = (wl["n"] + (1 << 20) - 1) >> 20
-    return sum(6 * chunks + (1 if c["fallback"] > 0 else 0) for c in wl["nfb"][-steps:])
+    return sum(6 * chunks + (2 if c["fallback"] > 0 else 0) for c in wl["nfb"][-steps:])
 
 
 def max_over_ranks(x, dist, device):

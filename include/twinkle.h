@@ -68,7 +68,13 @@ enum {
     TW_POS_IMAGECOUNT = 2, /* a limb sample had no image set with 3 or 5 real
                               images and parity sum -1 (Sec. 2.3) */
     TW_POS_NONFINITE = 4,  /* non-finite input position or result (out is NaN) */
-    TW_POS_SOLVER = 8      /* root iteration stopped at its iteration limit */
+    TW_POS_SOLVER = 8,     /* root iteration stopped at its iteration limit */
+    TW_POS_SLOPE = 16      /* a caustic crossing failed the slope test
+                              (Sec. 2.4.2): its pair of merging images was
+                              not perpendicular to the ghost pair across it;
+                              the crossing was moved to the slope jump, or a
+                              false image piece removed, where the walk along
+                              the five-image run found one */
 };
 
 /* Arithmetic modes. */
@@ -139,7 +145,9 @@ int tw_lightcurve_batch(const double *params, const int64_t *offsets, const doub
  * memory belongs to their own pool or arena, and real-time loops in which an
  * allocation could stall or fail.  (The paper has no counterpart: it
  * describes no API.)  It computes what tw_mag_ex computes, with the given
- * precision (TW_PREC_*) and sample cap max_samples (64..512), on `stream`.
+ * precision (TW_PREC_*) and sample cap max_samples (64..512), on `stream`,
+ * except the slope-repair pass: a crossing that fails the slope test is
+ * counted in no status (there is none) and not repaired.
  * y1, y2 and out must be device pointers of the current device; the call is
  * asynchronous.  The library's scratch for this entry point is one static
  * device array of about 53 MiB (608 warp arenas of 512 limb samples plus a
@@ -217,11 +225,11 @@ int tw_version(void);
  * paper has no counterpart (it reports no operation counts). */
 int tw_last_launch_work(int64_t out[5]);
 
-/* Device time, in milliseconds, of the most recent contour-integration kernel
- * launch on the current device (every entry point above that integrates
- * contours, including the fallback launch of tw_surrogate_mag), measured by
- * two CUDA events recorded on the launch's stream directly before and after
- * the kernel; waits for it.  TW_EINVAL if no launch has been timed.  No
+/* Device time, in milliseconds, of the most recent contour integration on
+ * the current device (every entry point above that integrates contours,
+ * including the fallback of tw_surrogate_mag): its main kernel and its
+ * slope-repair kernel, measured by two CUDA events recorded on the launch's
+ * stream directly before and after them; waits for it.  TW_EINVAL if no launch has been timed.  No
  * counterpart in the paper (a measurement hook of this library). */
 int tw_last_launch_ms(float *ms);
 
@@ -231,6 +239,22 @@ int tw_last_launch_ms(float *ms);
  * magnitude 1e-300..1e300: *rcp_max_rel_err receives the largest relative
  * difference.  Synchronous.  The paper has no counterpart. */
 int tw_selftest(double *rcp_max_rel_err);
+
+/* Device self-test of the slope test and its repair (Sec. 2.4.2) on a planted
+ * misjudgment.  The limb of the source (s, q <= 1, rho, centre y1, y2) is
+ * sampled at the n (8..256) host angles theta[] (ascending, in [0, 2 pi)),
+ * which must include closely spaced samples (steps < 1e-3) across a caustic
+ * crossing; every edge is linked and integrated.  Then the ghost pair of
+ * three-image samples next to that crossing is declared real: mode 1 the
+ * sample adjacent to the crossing (the crossing moves by one sample), mode 2
+ * the two samples beyond it (a false image piece).  out4[0] = 1 when the
+ * planted crossing failed the slope test, out4[1] = 1 when the repair gave
+ * back the original classification of every sample, out4[2] = relative
+ * change of the total area after the repair (-1 when no crossing was found),
+ * out4[3] = theta position of the crossing found (-1 none).  Synchronous;
+ * the paper has no counterpart (a test hook of this library). */
+int tw_selftest_slope(double s, double q, double rho, double y1, double y2, const double *theta, int n, int mode,
+                      double *out4);
 
 #ifdef __cplusplus
 }

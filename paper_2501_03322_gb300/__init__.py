@@ -26,7 +26,7 @@ import numpy as np
 from . import build as _build
 
 TW_OK, TW_EINVAL, TW_ECUDA, TW_ENOMEM, TW_ETIMEOUT, TW_ETOOBIG, TW_WCAP = 0, -1, -2, -3, -4, -5, 1
-POS_CAP, POS_IMAGECOUNT, POS_NONFINITE, POS_SOLVER = 1, 2, 4, 8
+POS_CAP, POS_IMAGECOUNT, POS_NONFINITE, POS_SOLVER, POS_SLOPE = 1, 2, 4, 8, 16
 PREC_FP64, PREC_MIXED = 0, 1
 
 _lock = threading.Lock()
@@ -89,6 +89,8 @@ def lib():
             L.tw_last_launch_work.restype = I
             L.tw_last_launch_ms.argtypes = [P]
             L.tw_last_launch_ms.restype = I
+            L.tw_selftest_slope.argtypes = [d, d, d, d, d, P, I, I, P]
+            L.tw_selftest_slope.restype = I
             L.tw_selftest.argtypes = [P]
             L.tw_selftest.restype = I
             L.tw_mag_noalloc.argtypes = [d, d, d, P, P, i64, d, P, I, I, P]
@@ -178,6 +180,15 @@ def last_launch_work() -> dict:
     a = np.zeros(5, np.int64)
     _check(lib().tw_last_launch_work(a.ctypes.data_as(ctypes.c_void_p)))
     return dict(samples=int(a[0]), sweeps64=int(a[1]), sweeps32=int(a[2]), edges=int(a[3]), newton64=int(a[4]))
+
+
+def selftest_slope(s, q, rho, y1, y2, theta, mode) -> dict:
+    """Device self-test of the slope test and repair on a planted misjudgment (tw_selftest_slope)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    out = np.zeros(4)
+    _check(lib().tw_selftest_slope(s, q, rho, y1, y2, th.ctypes.data_as(ctypes.c_void_p), int(th.size), int(mode),
+                                   out.ctypes.data_as(ctypes.c_void_p)))
+    return dict(detected=bool(out[0]), restored=bool(out[1]), area_change=float(out[2]), crossing=int(out[3]))
 
 
 def last_launch_ms() -> float:

@@ -33,7 +33,7 @@ namespace tw {
 constexpr unsigned FULL = 0xffffffffu;
 
 // Position status bits (mirrors TW_POS_* of twinkle.h).
-enum : int { PS_CAP = 1, PS_IMAGECOUNT = 2, PS_NONFINITE = 4, PS_SOLVER = 8 };
+enum : int { PS_CAP = 1, PS_IMAGECOUNT = 2, PS_NONFINITE = 4, PS_SOLVER = 8, PS_SLOPE = 16 };
 
 // One warp slot of the sample arena.  Records are indexed by sample slot (the
 // order in which samples were created); ordA/ordB hold slot numbers in theta
@@ -210,9 +210,72 @@ __device__ __forceinline__ Img load_img(const Arena &ar, int slot, uint32_t meta
     return m;
 }
 
+__device__ __forceinline__ unsigned real_mask(uint32_t meta) {
+    unsigned m = 0;
+    const int n = meta_count(meta);
+    for (int k = 0; k < n; k++) m |= 1u << meta_index(meta, k);
+    return m;
+}
+
+// Slope test (Sec. 2.4.2).  Near a critical curve the separation of the two
+// images that merge there is the square root of a quantity that changes sign
+// across the caustic, so the difference of the pair that is real on the
+// five-image side and the difference of the ghost pair on the three-image
+// side are perpendicular, while the differences of one pair at neighbouring
+// samples of the same side are nearly parallel.  The local form holds only
+// while both pairs are close compared with the other images.
+//
+// Relation of two pairs with differences d1, d2 whose midpoints lie at
+// squared distances o1, o2 from the nearest other image: +1 both local
+// (|d|^2 < o/16) and perpendicular (cos^2 < 1/4), -1 both local and parallel
+// (cos^2 > 0.81), 0 otherwise.
+__device__ __forceinline__ int pair_relation(cxf d1, float o1, cxf d2, float o2) {
+    const float n1 = norm2(d1), n2 = norm2(d2);
+    if (!(n1 < 0.0625f * o1 && n2 < 0.0625f * o2)) return 0;
+    const float c = dot(d1, d2), c2 = c * c, nn = n1 * n2;
+    return c2 < 0.25f * nn ? 1 : (c2 > 0.81f * nn ? -1 : 0);
+}
+
+// Pair (class slots kp, kn) of the five-image sample s5: difference P - M and
+// squared distance from its midpoint to the nearest other real image.
+__device__ __forceinline__ cxf pair5(const Arena &ar, int s5, uint32_t m5, int kp, int kn, float &o) {
+    const cxf P = to_f(ar.roots[s5 * 5 + meta_index(m5, kp)]), M = to_f(ar.roots[s5 * 5 + meta_index(m5, kn)]);
+    const cxf c = 0.5f * (P + M);
+    o = 3.0e38f;
+    for (int k = 0; k < 5; k++)
+        if (k != kp && k != kn) o = fminf(o, norm2(to_f(ar.roots[s5 * 5 + meta_index(m5, k)]) - c));
+    return P - M;
+}
+
+// Ghost pair of the three-image sample s3: difference and squared distance
+// from its midpoint to the nearest real image.
+__device__ __forceinline__ cxf ghost3(const Arena &ar, int s3, uint32_t m3, float &o) {
+    const unsigned real3 = real_mask(m3);
+    cxf G[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    int ng = 0;
+    for (int i = 0; i < 5; i++)
+        if (!((real3 >> i) & 1u) && ng < 2) G[ng++] = to_f(ar.roots[s3 * 5 + i]);
+    const cxf c = 0.5f * (G[0] + G[1]);
+    o = 3.0e38f;
+    for (int k = 0; k < 3; k++) o = fminf(o, norm2(to_f(ar.roots[s3 * 5 + meta_index(m3, k)]) - c));
+    return G[0] - G[1];
+}
+
+// Crossing at an edge: true when the extra pair of its five-image sample and
+// the ghost pair of its three-image sample are parallel, i.e. the crossing is
+// misplaced (a ghost pair was taken for real).
+__device__ __forceinline__ bool slope_violation(const Arena &ar, int s5, uint32_t m5, int kp, int kn, int s3,
+                                                uint32_t m3) {
+    float o5, o3;
+    const cxf d5 = pair5(ar, s5, m5, kp, kn, o5), d3 = ghost3(ar, s3, m3, o3);
+    return pair_relation(d5, o5, d3, o3) == -1;
+}
+
 // Area and error of the edge from sample slot sa to slot sb (angle step dth).
-static __device__ __noinline__ void compute_edge(const Arena &ar, int sa, int sb, double dth, double *outA, double *outE) {
-    const uint32_t ma = ar.meta[sa], mb = ar.meta[sb];
+// Returns PS_SLOPE when the edge is a caustic crossing that fails the slope
+// test.
+__device__ __forceinline__ void link_edge(const Arena &ar, int sa, int sb, uint32_t ma, uint32_t mb, uint64_t &links,
+                                          int &nlinks, int &lp, int &ln) {
     const int na = meta_count(ma), nb = meta_count(mb);
     cxd ZA[5], ZB[5];
 #pragma unroll
@@ -220,12 +283,21 @@ static __device__ __noinline__ void compute_edge(const Arena &ar, int sa, int sb
         if (k < na) ZA[k] = ar.roots[sa * 5 + meta_index(ma, k)];
         if (k < nb) ZB[k] = ar.roots[sb * 5 + meta_index(mb, k)];
     }
-    uint64_t links = 0;
-    int nlinks = 0, lp = -1, ln = -1;
+    links = 0;
+    nlinks = 0;
+    lp = ln = -1;
     if (na == 3 && nb == 3) edge_links<3, 3>(ZA, ZB, links, nlinks, lp, ln);
     else if (na == 5 && nb == 5) edge_links<5, 5>(ZA, ZB, links, nlinks, lp, ln);
     else if (na == 3) edge_links<3, 5>(ZA, ZB, links, nlinks, lp, ln);
     else edge_links<5, 3>(ZA, ZB, links, nlinks, lp, ln);
+}
+
+static __device__ __noinline__ int compute_edge(const Arena &ar, int sa, int sb, double dth, double *outA, double *outE) {
+    const uint32_t ma = ar.meta[sa], mb = ar.meta[sb];
+    const int na = meta_count(ma), nb = meta_count(mb);
+    uint64_t links;
+    int nlinks, lp, ln, flags = 0;
+    link_edge(ar, sa, sb, ma, mb, links, nlinks, lp, ln);
     double dA = 0.0;
     float dE = 0.0f;
     const float dthf = (float)dth;
@@ -240,12 +312,104 @@ static __device__ __noinline__ void compute_edge(const Arena &ar, int sa, int sb
         const int sl = creation ? sb : sa;
         const uint32_t ml = creation ? mb : ma;
         pair_contrib(load_img(ar, sl, ml, lp), load_img(ar, sl, ml, ln), creation, dthf, dA, dE);
+        if (slope_violation(ar, sl, ml, lp, ln, creation ? sa : sb, creation ? ma : mb)) flags |= PS_SLOPE;
     }
     double dEd = (double)dE;
     // a sample that failed the image-count check: keep refining around it
     if ((ma | mb) >> 31) dEd += fabs(dA);
     *outA = dA;
     *outE = dEd;
+    return flags;
+}
+
+// Repair of a crossing that failed the slope test, at the edge from theta
+// position p to p + 1 (ord: slots in theta order, N samples, cyclic), after
+// Sec. 2.4.2: starting at the crossing's five-image sample, the extra pair is
+// followed into the five-image run (at each sample the positive and negative
+// images nearest to the previous pair's) until
+//   - two consecutive pairs are perpendicular: the jump of the slope is there,
+//     and the samples before it carried a ghost pair taken for real; they are
+//     re-judged as three-image samples (the crossing moves to the jump);
+//   - the run ends at a three-image sample whose crossing also fails the
+//     test: the whole run is a false image piece and is re-judged.
+// Otherwise (pairs no longer close, a failed sample, 64 samples walked)
+// nothing is changed.  Re-judged samples carry meta bit 30 and are never
+// re-judged again; the edges around them are recomputed.  Runs on one lane.
+constexpr int SLOPE_WALK = 64;
+
+static __device__ __noinline__ int slope_fix(const Arena &ar, const uint16_t *ord, int N, int p) {
+    const double twopi = 6.283185307179586476925287;
+    auto slot = [&](int i) { return (int)ord[((i % N) + N) % N]; };
+    const int sa = slot(p), sb = slot(p + 1);
+    const uint32_t ma = ar.meta[sa], mb = ar.meta[sb];
+    if ((ma | mb) >> 30) return PS_SLOPE;
+    const int na = meta_count(ma), nb = meta_count(mb);
+    if (na == nb) return 0;
+    uint64_t links;
+    int nlinks, kp, kn;
+    link_edge(ar, sa, sb, ma, mb, links, nlinks, kp, kn);
+    const int dir = na == 5 ? -1 : 1;  // from the crossing into the five-image run
+    const int first = na == 5 ? p : p + 1;
+    uint8_t pk[SLOPE_WALK];  // pair (kp | kn << 3) of each walked sample
+    int len = 0, j = first, s5 = slot(first);
+    uint32_t m5 = ar.meta[s5];
+    bool rejudge = false;
+    for (;;) {
+        pk[len++] = (uint8_t)(kp | (kn << 3));
+        float o;
+        const cxf d = pair5(ar, s5, m5, kp, kn, o);
+        const cxf P = to_f(ar.roots[s5 * 5 + meta_index(m5, kp)]), M = to_f(ar.roots[s5 * 5 + meta_index(m5, kn)]);
+        const int sn = slot(j + dir);
+        const uint32_t mn = ar.meta[sn];
+        if (mn >> 30) return PS_SLOPE;
+        if (meta_count(mn) == 3) {
+            // the far end of the run: a false piece when that crossing fails too
+            float o3;
+            const cxf d3 = ghost3(ar, sn, mn, o3);
+            rejudge = pair_relation(d, o, d3, o3) == -1;
+            break;
+        }
+        // the next sample's pair: positive image nearest P, negative nearest M
+        int np = 0, nn = 2;
+        float bp = 3.0e38f, bn = 3.0e38f;
+        for (int k = 0; k < 5; k++) {
+            const cxf z = to_f(ar.roots[sn * 5 + meta_index(mn, k)]);
+            if (k < 2) { const float t = norm2(z - P); if (t < bp) { bp = t; np = k; } }
+            else { const float t = norm2(z - M); if (t < bn) { bn = t; nn = k; } }
+        }
+        float on;
+        const cxf dn = pair5(ar, sn, mn, np, nn, on);
+        const int rel = pair_relation(d, o, dn, on);
+        if (rel == 1) { rejudge = true; break; }  // the jump
+        if (rel == 0 || len == SLOPE_WALK || len >= N - 2) break;
+        j += dir;
+        s5 = sn;
+        m5 = mn;
+        kp = np;
+        kn = nn;
+    }
+    if (!rejudge) return PS_SLOPE;
+    // re-judge the walked samples: drop their pair, keep the other three images
+    for (int t = 0; t < len; t++) {
+        const int sl = slot(first + dir * t);
+        const uint32_t m = ar.meta[sl];
+        const int a = pk[t] & 7, b = pk[t] >> 3;
+        uint32_t nm = 3u | (1u << 30);
+        int k3 = 0;
+        for (int k = 0; k < 5; k++)
+            if (k != a && k != b) { nm |= (uint32_t)meta_index(m, k) << (3 + 3 * k3); k3++; }
+        ar.meta[sl] = nm;
+    }
+    // recompute the edges touching them
+    const int lo = dir > 0 ? first - 1 : first - len;
+    int flags = PS_SLOPE;
+    for (int e = lo; e <= lo + len; e++) {
+        const int ee = ((e % N) + N) % N;
+        const int s0 = ord[ee], s1 = ord[(ee + 1) % N];
+        const double t1 = (ee + 1 < N) ? ar.theta[s1] : ar.theta[s1] + twopi;
+        compute_edge(ar, s0, s1, t1 - ar.theta[s0], &ar.eA[s0], &ar.eE[s0]);
+    }
+    return flags;
 }
 
 // One limb sample: coefficients, roots (warm-started from z), classification,
@@ -271,13 +435,6 @@ __device__ __forceinline__ void predict_roots(cxd z[5], const cxf dz[5], unsigne
             if (j != i) sep2 = fminf(sep2, norm2(zf[i] - zf[j]));
         if (norm2(dz[i]) < 0.04f * sep2) z[i] = z[i] + to_d(dz[i]);
     }
-}
-
-__device__ __forceinline__ unsigned real_mask(uint32_t meta) {
-    unsigned m = 0;
-    const int n = meta_count(meta);
-    for (int k = 0; k < n; k++) m |= 1u << meta_index(meta, k);
-    return m;
 }
 
 template <int PREC>
@@ -308,7 +465,28 @@ struct PosResult {
     WorkCount work;  // summed over the warp
 };
 
-template <int PREC, int SPL>
+// Repairs (one lane at a time) of the crossings that failed the slope test:
+// vpos is this lane's edge position, or -1.  Returns status bits (the same on
+// every lane).
+static __device__ __noinline__ int slope_repairs(const Arena &ar, const uint16_t *ord, int N, int vpos) {
+    const int lane = threadIdx.x & 31;
+    unsigned vb = __ballot_sync(FULL, vpos >= 0);
+    int f = 0;
+    while (vb) {
+        const int src = __ffs(vb) - 1;
+        const int p = __shfl_sync(FULL, vpos, src);
+        if (lane == 0) f |= slope_fix(ar, ord, N, p);
+        __syncwarp();
+        vb &= vb - 1;
+    }
+    return __shfl_sync(FULL, f, 0);
+}
+
+// REPAIR = false: a crossing that fails the slope test only sets PS_SLOPE
+// (the position is then integrated again by the REPAIR = true instance, which
+// repairs such crossings as they appear).  Keeping the repair code out of the
+// main instance keeps its register allocation unchanged.
+template <int PREC, int SPL, bool REPAIR>
 __device__ PosResult integrate_position(const LensK &L, double tol, int cap, const Arena &ar, WarpStage &ws) {
     constexpr int SPI = 32 * SPL;
     const int lane = threadIdx.x & 31;
@@ -316,6 +494,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
     const double minsep = 1e-15 / L.rho + 1e-14;
     int flags = 0;
     WorkCount wc;
+    int vpos = -1;  // theta position of an edge that failed the slope test
 
     // Images of a point inside the source: the warm start of the first samples.
     // The point is offset from the centre by rho/2 because Eq. 6 degenerates
@@ -417,7 +596,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
 #pragma unroll
     for (int t = 0; t < SPL; t++) {
         const int k = lane * SPL + t;
-        compute_edge(ar, k, (k + 1 == SPI) ? 0 : k + 1, twopi / SPI, &ar.eA[k], &ar.eE[k]);
+        if (compute_edge(ar, k, (k + 1 == SPI) ? 0 : k + 1, twopi / SPI, &ar.eA[k], &ar.eE[k])) vpos = k;
         wc.edges++;
     }
     __syncwarp();
@@ -426,6 +605,13 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
     uint16_t *ordA = ar.ordA, *ordB = ar.ordB;
     double A = 0.0, E = 0.0;
     for (;;) {
+        // crossings of the last edges that failed the slope test (rare)
+        if (REPAIR) {
+            if (__any_sync(FULL, vpos >= 0)) flags |= slope_repairs(ar, ordA, N, vpos);
+        } else if (vpos >= 0) {
+            flags |= PS_SLOPE;
+        }
+        vpos = -1;
         double a = 0.0, e = 0.0;
         for (int p = lane; p < N; p += 32) {
             const int sl = ordA[p];
@@ -559,16 +745,17 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
                 const int nx = (P + 1 < N) ? P + 1 : 0;
                 const int sb = ordA[nx];
                 const double tb = (P + 1 < N) ? ar.theta[sb] : twopi;
-                compute_edge(ar, sl, sb, tb - tn[t], &ar.eA[sl], &ar.eE[sl]);
+                if (compute_edge(ar, sl, sb, tb - tn[t], &ar.eA[sl], &ar.eE[sl])) vpos = P;
                 wc.edges++;
                 const bool first = (rk[t] == 0) || (ws.pos_new[rk[t] - 1] != tp[t]);
                 if (first) {
                     const int so = ordA[P - 1];
-                    compute_edge(ar, so, sl, tn[t] - ar.theta[so], &ar.eA[so], &ar.eE[so]);
+                    if (compute_edge(ar, so, sl, tn[t] - ar.theta[so], &ar.eA[so], &ar.eE[so])) vpos = P - 1;
                     wc.edges++;
                 }
             }
         __syncwarp();
+
     }
     flags = __reduce_or_sync(FULL, flags);
     PosResult r;

@@ -57,7 +57,9 @@ struct KParams {
     double tol;
     int chunk;                    // consecutive work items taken per atomic grab
     unsigned long long *counter;  // [0]: next work item; [1..5]: samples, FP64 sweeps, FP32 sweeps, edges,
-                                  // FP64 Newton passes
+                                  // FP64 Newton passes; [6]: queued repairs; [7]: next repair item
+    int64_t *relist;              // work items queued for the repair pass (or null: no repairs)
+    unsigned long long relist_cap;
 };
 
 struct PosIn {
@@ -106,22 +108,28 @@ __device__ __forceinline__ bool fetch_position(const WorkSrc &w, int64_t idx, Po
            pos_ok(P.y1) && pos_ok(P.y2);
 }
 
-template <int PREC, int SPL>
+// REPAIR = false: the main pass over src.n work items.  REPAIR = true: the
+// repair pass over the work items that the main pass queued in kp.relist
+// (crossings that failed the slope test), integrated again with repairs.
+template <int PREC, int SPL, bool REPAIR>
 __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParams kp) {
     __shared__ WarpStage stage[WPB];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * WPB + wib;
     const Arena ar = arena_at(kp.arena, kp.slot_bytes, kp.cap, gw);
-    unsigned long long idx = 0, end = 0;
+    unsigned long long n = (unsigned long long)kp.src.n;
+    if (REPAIR) n = min(*(volatile unsigned long long *)(kp.counter + 6), kp.relist_cap);
+    unsigned long long it = 0, end = 0, idx = 0;
     for (;;) {
-        if (idx >= end) {
+        if (it >= end) {
             unsigned long long first = 0;
-            if (lane == 0) first = atomicAdd(kp.counter, (unsigned long long)kp.chunk);
-            idx = __shfl_sync(FULL, first, 0);
-            end = idx + (unsigned long long)kp.chunk;
-            if (end > (unsigned long long)kp.src.n) end = (unsigned long long)kp.src.n;
-            if (idx >= end) break;
+            if (lane == 0) first = atomicAdd(kp.counter + (REPAIR ? 7 : 0), (unsigned long long)kp.chunk);
+            it = __shfl_sync(FULL, first, 0);
+            end = it + (unsigned long long)kp.chunk;
+            if (end > n) end = n;
+            if (it >= end) break;
         }
+        idx = REPAIR ? (unsigned long long)kp.relist[it] : it;
         PosIn P;
         const bool valid = fetch_position(kp.src, (int64_t)idx * kp.src.stride, P);
         double mu = __longlong_as_double(0x7ff8000000000000ll), err = mu;
@@ -139,7 +147,13 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParam
             L.m2 = q * L.m1;
             L.rho = P.rho;
             L.y0 = {y1 - P.s * L.m1, P.y2};  // centre-of-mass -> secondary frame
-            const PosResult r = integrate_position<PREC, SPL>(L, kp.tol, kp.cap, ar, stage[wib]);
+            const PosResult r = integrate_position<PREC, SPL, REPAIR>(L, kp.tol, kp.cap, ar, stage[wib]);
+            // a crossing failed the slope test: queue the position for the
+            // repair pass (its outputs below are overwritten there)
+            if (!REPAIR && (r.status & PS_SLOPE) && kp.relist && lane == 0) {
+                const unsigned long long k = atomicAdd(kp.counter + 6, 1ull);
+                if (k < kp.relist_cap) kp.relist[k] = (int64_t)idx;
+            }
             const double inv_src = rcp(3.141592653589793238 * P.rho * P.rho);
             mu = r.area * inv_src;
             err = r.err * inv_src;
@@ -161,7 +175,7 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParam
             if (kp.nsamp) kp.nsamp[o] = nsamp;
             if (kp.pstat) kp.pstat[o] = (int8_t)status;
         }
-        idx++;
+        it++;
     }
 }
 
@@ -169,11 +183,18 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParam
 // Host launcher and occupancy query of one kernel instance.
 #define TW_DEFINE_LAUNCHER(PREC, SPL)                                                              \
     cudaError_t launch_contour_##PREC##_##SPL(unsigned blocks, cudaStream_t st, const KParams &kp) { \
-        contour_kernel<PREC, SPL><<<blocks, TPB, 0, st>>>(kp);                                      \
+        contour_kernel<PREC, SPL, false><<<blocks, TPB, 0, st>>>(kp);                               \
         return cudaGetLastError();                                                                  \
     }                                                                                               \
     cudaError_t occupancy_contour_##PREC##_##SPL(int *occ) {                                        \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, contour_kernel<PREC, SPL>, TPB, 0); \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, contour_kernel<PREC, SPL, false>, TPB, 0); \
+    }
+
+// The repair-pass instance of a precision (two samples per lane).
+#define TW_DEFINE_REPAIR_LAUNCHER(PREC)                                                            \
+    cudaError_t launch_repair_##PREC(unsigned blocks, cudaStream_t st, const KParams &kp) {       \
+        contour_kernel<PREC, 2, true><<<blocks, TPB, 0, st>>>(kp);                                 \
+        return cudaGetLastError();                                                                 \
     }
 
 #define TW_DECLARE_LAUNCHER(PREC, SPL)                                                           \
@@ -196,5 +217,7 @@ TW_DECLARE_LAUNCHER(0, 4)
 TW_DECLARE_LAUNCHER(1, 1)
 TW_DECLARE_LAUNCHER(1, 2)
 TW_DECLARE_LAUNCHER(1, 4)
+cudaError_t launch_repair_0(unsigned blocks, cudaStream_t st, const KParams &kp);
+cudaError_t launch_repair_1(unsigned blocks, cudaStream_t st, const KParams &kp);
 
 }  // namespace tw

@@ -45,6 +45,8 @@ struct DevState {
     cudaEvent_t last = nullptr;     // completion of the previous launch (serialises calls)
     cudaEvent_t t0 = nullptr, t1 = nullptr;  // timing events around the latest kernel launch
     bool timed = false;             // t0/t1 hold a launch
+    int64_t *relist = nullptr;      // work items queued for the slope-repair pass
+    size_t relist_bytes = 0;
     char *calib = nullptr;          // outputs of autotuning calibration runs
     size_t calib_bytes = 0;
     cudaGraphExec_t graph = nullptr;  // replayable {counter reset, persistent kernel}
@@ -141,6 +143,10 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     const size_t slot_bytes = arena_slot_bytes(cap);
     int rc = grow(&d.arena, &d.arena_bytes, slot_bytes * (size_t)blocks * WPB);
     if (rc) return rc;
+    // repair queue: room for every work item up to 2^20 (positions beyond it
+    // that fail the slope test keep the main pass's result and PS_SLOPE)
+    const size_t relist_cap = (size_t)(src.n < (1 << 20) ? (src.n > 0 ? src.n : 1) : (1 << 20));
+    if ((rc = grow((char **)&d.relist, &d.relist_bytes, relist_cap * sizeof(int64_t)))) return rc;
     // serialise with the previous launch (the arena and counter are shared)
     if ((e = cudaStreamWaitEvent(st, d.last, 0)) != cudaSuccess) return cuda_fail(e);
     KParams kp;
@@ -155,13 +161,24 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     kp.tol = tol;
     kp.chunk = cfg.chunk < 1 ? 1 : cfg.chunk;
     kp.counter = d.counter;
+    kp.relist = d.relist;
+    kp.relist_cap = d.relist_bytes / sizeof(int64_t);
+    // main pass, then the repair pass over the items it queued (usually none:
+    // the repair kernel finds an empty queue and exits)
+    auto kernels = [&]() -> cudaError_t {
+        cudaError_t e0 = lf((unsigned)blocks, st, kp);
+        if (e0 != cudaSuccess) return e0;
+        // at most as many warps as the arena has slots
+        const unsigned rblocks = (unsigned)(blocks < d.nsm ? blocks : d.nsm);
+        return (prec == TW_PREC_FP64 ? launch_repair_0 : launch_repair_1)(rblocks, st, kp);
+    };
     bool graphed = false;
     if (use_graph && st != nullptr) {
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = cudaMemsetAsync(d.counter, 0, 6 * sizeof(unsigned long long), st);
-            cudaError_t e2 = lf((unsigned)blocks, st, kp);
+            cudaError_t e1 = cudaMemsetAsync(d.counter, 0, 8 * sizeof(unsigned long long), st);
+            cudaError_t e2 = kernels();
             e = cudaStreamEndCapture(st, &g);
             if (e == cudaSuccess && e1 == cudaSuccess && e2 == cudaSuccess) {
                 bool ok = false;
@@ -182,9 +199,9 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
         (void)cudaGetLastError();
     }
     if (!graphed) {
-        if ((e = cudaMemsetAsync(d.counter, 0, 6 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaMemsetAsync(d.counter, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_fail(e);
         d.timed = cudaEventRecord(d.t0, st) == cudaSuccess;
-        if ((e = lf((unsigned)blocks, st, kp)) != cudaSuccess) { d.timed = false; return cuda_fail(e); }
+        if ((e = kernels()) != cudaSuccess) { d.timed = false; return cuda_fail(e); }
         d.timed = d.timed && cudaEventRecord(d.t1, st) == cudaSuccess;
     }
     (void)cudaGetLastError();

@@ -199,3 +199,34 @@ def test_mag_multi_per_position_lens(prec):
     ok = np.array([int(r[6]) == 0 for r in rows])
     mu = P.mag_multi(a[:, 0], a[:, 1], a[:, 2], a[:, 3], a[:, 4], rel_tol=TOL, precision=prec)
     assert rel_err(mu[ok], a[ok, 5]).max() <= TOL
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("cfg", [(1.0, 0.1, 0.1, 0.2, 0.2), (0.5, 1e-6, 1e-4, -1.49981640625, 0.0035)])
+def test_slope_test_repairs_planted_misjudgment(cfg, mode):
+    """Sec. 2.4.2 on the device: samples crowded around a caustic crossing the
+    oracle located; a ghost pair next to the crossing (mode 1) or a false
+    two-sample piece beyond it (mode 2) is planted as real, must fail the slope
+    test, and the repair must restore every sample and the area."""
+    import oracle as O
+
+    s, q, rho, y1, y2 = cfg
+    xs = O.crossings(s, q, rho, y1, y2)
+    gap = min(np.diff(np.r_[xs, xs[0] + 2 * np.pi]))
+    h = min(1e-5, 1e-3 * gap)
+    fine = xs[0] + (np.arange(-8, 8) + 0.5) * h
+    coarse = np.linspace(0, 2 * np.pi, 48, endpoint=False)
+    coarse = coarse[np.abs((coarse - xs[0] + np.pi) % (2 * np.pi) - np.pi) > 40 * h]
+    theta = np.sort(np.r_[coarse, fine % (2 * np.pi)])
+    r = P.selftest_slope(s, q, rho, y1, y2, theta, mode)
+    assert r["crossing"] >= 0, r
+    assert r["detected"] and r["restored"] and 0 <= r["area_change"] <= 1e-12, r
+
+
+def test_slope_test_quiet_on_map():
+    """No caustic crossing of the planetary-caustic map fails the slope test:
+    the residual test with its round-off gate already classifies them."""
+    c = W.MAP_PLANETARY
+    y1, y2 = W.map_grid()
+    mu, err, ns, st = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(y2), rel_tol=c["rel_tol"], details=True)
+    assert int(((st.cpu().numpy() & P.POS_SLOPE) != 0).sum()) == 0

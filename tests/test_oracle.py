@@ -220,3 +220,38 @@ def test_trajectory_geometry():
     d = np.array([y1[2] - y1[1], y2[2] - y2[1]])
     assert abs(math.atan2(d[1], d[0]) - alpha) < 1e-14
     assert abs(np.hypot(*d) - 1) < 1e-14
+
+
+def _merging_pairs(s, q, zeta0, rho, theta, dth):
+    """Differences of the pair that is real on the five-image side of a
+    crossing at limb angle theta (positive minus negative parity, the closest
+    such pair) and of the ghost pair on its three-image side."""
+    side = [O.images(s, q, zeta0 + rho * np.exp(1j * (theta + d))) for d in (-dth, dth)]
+    five = side[0] if side[0]["count"] == 5 else side[1]
+    three = side[1] if five is side[0] else side[0]
+    assert five["count"] == 5 and three["count"] == 3
+    R, J = five["roots"][five["real"]], five["jac"][five["real"]]
+    pairs = [(abs(R[a] - R[b]), R[a] - R[b]) for a in range(5) for b in range(5) if J[a] > 0 > J[b]]
+    d5 = min(pairs, key=lambda t: t[0])[1]
+    g = three["roots"][~three["real"]]
+    return d5, g[0] - g[1]
+
+
+@pytest.mark.parametrize("cfg", [(1.0, 0.1, 0.1, 0.2, 0.2), (0.5, 1e-6, 1e-4, -1.49981640625, 0.0035)])
+def test_slope_premise(cfg):
+    """Sec. 2.4.2: across a caustic crossing the merging real pair and the ghost
+    pair are perpendicular, with equal separations to leading order (the
+    separation is the square root of a quantity that changes sign), and the
+    real pair keeps its direction from one sample to the next."""
+    s, q, rho, y1, y2 = cfg
+    z0 = complex(y1, y2)
+    xs = O.crossings(s, q, rho, y1, y2)
+    gap = min(np.diff(np.r_[xs, xs[0] + 2 * np.pi]))
+    h = min(1e-4, 1e-3 * gap)  # well inside the local (fold) regime of each crossing
+    for th in xs:
+        for dth in (h / 100, h):
+            d5, d3 = _merging_pairs(s, q, z0, rho, th, dth)
+            cos = abs((d5 * np.conj(d3)).real) / (abs(d5) * abs(d3))
+            assert cos < 1e-2 and abs(abs(d5) / abs(d3) - 1) < 1e-2, (th, dth, cos)
+            e5, _ = _merging_pairs(s, q, z0, rho, th, 2 * dth)
+            assert abs((d5 * np.conj(e5)).real) / (abs(d5) * abs(e5)) > 0.99
