@@ -27,6 +27,12 @@ LIGHTCURVE_CENTRAL = dict(s=1.0, q=1e-3, rho=1e-3, u0=0.01, alpha=1.0, t0=0.0, t
 MAP_PLANETARY = dict(s=0.8, q=1e-4, rho=5e-4, centre=(-0.44985, 0.016993), half=0.05, n=512, rel_tol=1e-4)
 STRESS_RESONANT = dict(s=1.0, q=0.5, rho=0.05, radius=0.6, n=1_000_000, rel_tol=1e-5, seed=2)
 BATCH_LIGHTCURVES = dict(ncurve=4096, nmin=200, nmax=5000, rel_tol=1e-4, seed=0)
+# Source centres on the tiny central caustic of a wide planetary lens: a disc
+# of radius 2e-4 around the primary lens (x = -q s/(1+q) for s=3, q=1e-4), a
+# source radius comparable to the caustic, magnifications up to ~1e4.  The
+# limb crosses the caustic next to its cusps, where ghost pairs come close.
+CENTRAL_WIDE = dict(s=3.0, q=1e-4, rho=1.1e-4, centre=(-2.9997000299970003e-4, 0.0), radius=2e-4, n=4096,
+                    rel_tol=1e-4, seed=5)
 
 
 def lightcurve_central_times(n: int = 1000) -> np.ndarray:
@@ -76,3 +82,12 @@ def sample_indices(n_total: int, k: int, seed: int = 12345) -> np.ndarray:
     """k distinct indices of range(n_total), sorted (seeded)."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(n_total, size=min(k, n_total), replace=False))
+
+
+def central_wide_positions(n=CENTRAL_WIDE["n"], centre=CENTRAL_WIDE["centre"], radius=CENTRAL_WIDE["radius"],
+                           seed=CENTRAL_WIDE["seed"]):
+    """Seeded positions uniform in a disc (the central-caustic set)."""
+    rng = np.random.default_rng(seed)
+    r = radius * np.sqrt(rng.uniform(size=n))
+    a = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    return centre[0] + r * np.cos(a), centre[1] + r * np.sin(a)

@@ -13,6 +13,7 @@ Files (text, one position per line: inputs, mu, oracle status):
   batch_lightcurves.txt   192 sampled (curve, time) points of the 4096-curve batch
   paper_worked.txt        the paper's worked configurations (Fig. 1, 2, 5)
   surrogate_queries.txt   192 positions near the caustics of 8 lenses of the surrogate's range
+  central_wide.txt        4096 centres on the central caustic of a wide planetary lens
 """
 from __future__ import annotations
 
@@ -168,7 +169,19 @@ def surrogate_queries():
     _write("surrogate_queries.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
 
 
-ALL = {"lightcurve_central": lightcurve_central, "surrogate_queries": surrogate_queries, "map_planetary": map_planetary, "stress_resonant": stress_resonant,
+def central_wide():
+    """All 4096 positions of the central-caustic set (wide planetary lens,
+    source radius comparable to the caustic)."""
+    c = W.CENTRAL_WIDE
+    y1, y2 = W.central_wide_positions()
+    mu, st, nx = O.mag(c["s"], c["q"], c["rho"], y1, y2, scan_K=256, nthreads=os.cpu_count())
+    hdr = ("Central caustic of a wide planetary lens: s=3, q=1e-4, rho=1.1e-4; 4096 centres uniform in a disc of\n"
+           "radius 2e-4 about the primary (seed 5); oracle magnifications.")
+    _write("central_wide.txt", hdr, ["i", "y1", "y2", "mu", "status", "ncross"],
+           zip(range(y1.size), y1, y2, mu, st, nx))
+
+
+ALL = {"lightcurve_central": lightcurve_central, "central_wide": central_wide, "surrogate_queries": surrogate_queries, "map_planetary": map_planetary, "stress_resonant": stress_resonant,
        "batch_lightcurves": batch_lightcurves, "paper_worked": paper_worked}
 
 if __name__ == "__main__":
