@@ -172,7 +172,7 @@ __global__ void sur_sample_kernel(uint64_t seed, int64_t n, double *S, double *Q
 // residual pair test (Sec. 2.4.1) and, for the real images, sum 1/|J| and
 // min |J| (Eq. 7).
 template <bool FP64>
-__device__ int point_images(const LensK &L, cxd y, cxd z[5], double &mu_ps, double &minJ) {
+static __device__ __noinline__ int point_images(const LensK &L, cxd y, cxd z[5], double &mu_ps, double &minJ) {
     cxd c[6];
     eq6_coeffs(L.s, L.m2, y, c);
     float ca[6];
@@ -324,7 +324,7 @@ __device__ bool caustic_within(float s, float m2, float m1, cxf y0, float reach)
 }
 
 // Raw features, point-source magnification and near-caustic flag per query.
-__global__ void sur_features_kernel(int64_t n, const double *S, const double *Q, const double *RHO, const double *Y1,
+__global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const double *S, const double *Q, const double *RHO, const double *Y1,
                                     const double *Y2, float *X, double *MUPS, uint8_t *FLAG, float *HEXE) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;

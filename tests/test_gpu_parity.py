@@ -230,3 +230,24 @@ def test_slope_test_quiet_on_map():
     y1, y2 = W.map_grid()
     mu, err, ns, st = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(y2), rel_tol=c["rel_tol"], details=True)
     assert int(((st.cpu().numpy() & P.POS_SLOPE) != 0).sum()) == 0
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_central_caustic_set_with_slope_repairs(prec):
+    """4096 centres on the tiny central caustic of a wide planet (source radius
+    comparable to the caustic): every position against the oracle, including
+    those where a crossing failed the slope test and was repaired (Sec. 2.4.2)."""
+    c = W.CENTRAL_WIDE
+    rows = load("central_wide.txt")
+    y1 = np.array([float(r[1]) for r in rows])
+    y2 = np.array([float(r[2]) for r in rows])
+    ref = np.array([float(r[3]) for r in rows])
+    ok = np.array([int(r[4]) == 0 for r in rows])
+    mu, err, ns, st = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(y2), rel_tol=c["rel_tol"], precision=prec,
+                            details=True)
+    mu, st = mu.cpu().numpy(), st.cpu().numpy()
+    e = rel_err(mu[ok], ref[ok])
+    slope = (st & P.POS_SLOPE) != 0
+    assert e.max() <= TOL, (e.max(), int(np.argmax(e)))
+    assert slope.sum() >= 1  # the repair pass is exercised on this set
+    assert rel_err(mu[ok & slope], ref[ok & slope]).max() <= TOL
