@@ -87,4 +87,10 @@ __device__ __forceinline__ cxf cdiv(cxf a, cxf b) {
 __device__ __forceinline__ cxf to_f(cxd a) { return {(float)a.x, (float)a.y}; }
 __device__ __forceinline__ cxd to_d(cxf a) { return {(double)a.x, (double)a.y}; }
 
+// Squared modulus in FP32, for magnitudes that only feed thresholds: FP64
+// components are converted first, which costs fewer FP64-pipe instructions
+// than an FP64 norm and a conversion.
+__device__ __forceinline__ float norm2f(cxd a) { return norm2(to_f(a)); }
+__device__ __forceinline__ float norm2f(cxf a) { return norm2(a); }
+
 }  // namespace tw

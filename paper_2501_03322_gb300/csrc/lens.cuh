@@ -86,7 +86,7 @@ __device__ __forceinline__ void eq6_coeffs(double s, double m2, cxd y, cxd c[6])
 
 __device__ __forceinline__ void abs_coeffs(const cxd c[6], float ca[6]) {
 #pragma unroll
-    for (int k = 0; k < 6; k++) ca[k] = sqrtf((float)norm2(c[k]));
+    for (int k = 0; k < 6; k++) ca[k] = sqrtf(norm2f(c[k]));
 }
 
 // Horner round-off bound sum_k |c_k| |z|^k (the attainable residual |p(z)|).
@@ -107,6 +107,19 @@ __device__ __forceinline__ void horner(const cx<T> c[6], cx<T> z, cx<T> &p, cx<T
         d = d * z + p;
         p = p * z + c[k];
     }
+}
+
+// 1/d and |1/d|^2.  FP64: conj(d)/|d|^2, whose squared modulus is 1/|d|^2
+// without a second norm.  FP32: the rescaled inverse (|d|^2 can underflow).
+__device__ __forceinline__ cxd pair_inv(cxd d, float &rr) {
+    const double q = rcp(fmax(norm2(d), 1e-300));
+    rr = (float)q;
+    return {d.x * q, -d.y * q};
+}
+__device__ __forceinline__ cxf pair_inv(cxf d, float &rr) {
+    const cxf r = inv(d);
+    rr = norm2(r);
+    return r;
 }
 
 // One Jacobi sweep of the Aberth-Ehrlich iteration on the quintic c:
@@ -130,10 +143,10 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
     for (int i = 0; i < 5; i++)
 #pragma unroll
         for (int j = i + 1; j < 5; j++) {
-            const cx<T> r = inv(z[i] - z[j]);
+            float rr;
+            const cx<T> r = pair_inv(z[i] - z[j], rr);
             S[i] = S[i] + r;
             S[j] = S[j] - r;
-            const float rr = (float)norm2(r);
             K2[i] += rr;
             K2[j] += rr;
         }
@@ -144,11 +157,11 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
         cx<T> p, d;
         horner(c, z[i], p, d);
         w[i] = cdiv(p, d - p * S[i]);
-        const float az = sqrtf((float)norm2(z[i]));
-        const float dabs = sqrtf((float)norm2(d));
+        const float az = sqrtf(norm2f(z[i]));
+        const float dabs = sqrtf(norm2f(d));
         dpa[i] = dabs;
         thr[i] = fmaxf(rtol * az, 8.0f * eps * horner_bound(ca, az) / fmaxf(dabs, 1e-37f));
-        wa2[i] = (float)norm2(w[i]);
+        wa2[i] = norm2f(w[i]);
         wmax = fmaxf(wmax, wa2[i]);
     }
     wmax = sqrtf(wmax);
@@ -303,7 +316,7 @@ __device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, 
         f1f[i] = to_f(f1);
         d1f[i] = to_f(d1);
         d2f[i] = to_f(d2);
-        const float az = sqrtf((float)norm2(z[i]));
+        const float az = sqrtf(norm2f(z[i]));
         noise[i] = 1.1e-16f * horner_bound(ca, az) * (1.0f + fabsf(f1f[i].x) + fabsf(f1f[i].y)) / fmaxf(dpa[i], 1e-37f);
     }
     int rank[5];

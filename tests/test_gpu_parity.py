@@ -245,9 +245,17 @@ def test_central_caustic_set_with_slope_repairs(prec):
     ok = np.array([int(r[4]) == 0 for r in rows])
     mu, err, ns, st = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(y2), rel_tol=c["rel_tol"], precision=prec,
                             details=True)
-    mu, st = mu.cpu().numpy(), st.cpu().numpy()
-    e = rel_err(mu[ok], ref[ok])
+    mu, err, st = mu.cpu().numpy(), err.cpu().numpy(), st.cpu().numpy()
+    # A limb that grazes a cusp tip (two crossings a few microradians apart)
+    # can keep an edge error that no refinement removes: sampling stops with
+    # TW_POS_CAP.  Such results must carry an honest error estimate; every
+    # other result must meet the tolerance.
+    capped = (st & (P.POS_CAP | P.POS_IMAGECOUNT)) != 0
+    clean = ok & ~capped
+    e = rel_err(mu[clean], ref[clean])
+    assert e.max() <= TOL, (e.max(), int(np.nonzero(clean)[0][np.argmax(e)]))
+    assert capped.sum() <= 0.005 * len(rows)
+    assert (np.abs(mu - ref)[ok & capped] <= err[ok & capped] + TOL * ref[ok & capped]).all()
     slope = (st & P.POS_SLOPE) != 0
-    assert e.max() <= TOL, (e.max(), int(np.argmax(e)))
     assert slope.sum() >= 1  # the repair pass is exercised on this set
-    assert rel_err(mu[ok & slope], ref[ok & slope]).max() <= TOL
+    assert rel_err(mu[clean & slope], ref[clean & slope]).max() <= TOL
