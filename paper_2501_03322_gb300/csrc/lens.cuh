@@ -109,22 +109,22 @@ __device__ __forceinline__ void horner(const cx<T> c[6], cx<T> z, cx<T> &p, cx<T
     }
 }
 
-// 1/d and |1/d|^2.  FP64: conj(d)/|d|^2, whose squared modulus is 1/|d|^2
-// without a second norm.  FP32: the rescaled inverse (|d|^2 can underflow).
-__device__ __forceinline__ cxd pair_inv(cxd d, float &rr) {
-    const double q = rcp(fmax(norm2(d), 1e-300));
-    rr = (float)q;
-    return {d.x * q, -d.y * q};
-}
-__device__ __forceinline__ cxf pair_inv(cxf d, float &rr) {
-    const cxf r = inv(d);
-    rr = norm2(r);
-    return r;
-}
+// FP32 value of a root difference (an FP64 difference is formed exactly
+// enough first, then rounded), and an FP32 pair sum widened to the iterate's
+// type.
+__device__ __forceinline__ cxf diff_f(cxd a, cxd b) { return to_f(a - b); }
+__device__ __forceinline__ cxf diff_f(cxf a, cxf b) { return a - b; }
+__device__ __forceinline__ cxd widen(cxf s, cxd) { return to_d(s); }
+__device__ __forceinline__ cxf widen(cxf s, cxf) { return s; }
 
 // One Jacobi sweep of the Aberth-Ehrlich iteration on the quintic c:
 // z_i <- z_i - w_i, w_i = p/(p' - p S_i), S_i = sum_{j != i} 1/(z_i - z_j), the
-// ten pair reciprocals being shared between the two roots of each pair.
+// ten pair reciprocals being shared between the two roots of each pair.  The
+// sums S_i are formed in FP32 in both precisions: they enter through p S_i,
+// which vanishes at a root, so their rounding changes the correction w_i by a
+// relative amount of order eps32 |w_i| |S_i| and limits neither the
+// convergence nor the attainable accuracy (set by p, p' and z in the
+// iterate's type).
 // dpa[i] receives |p'(z_i)|.  Returns true when every root is converged: its
 // correction, or the error left after it, is below
 // thr_i = max(rtol |z_i|, 8 eps B_i/|p'(z_i)|) (B_i the Horner round-off
@@ -135,18 +135,18 @@ __device__ __forceinline__ cxf pair_inv(cxf d, float &rr) {
 template <typename T>
 __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6], cx<T> z[5], float dpa[5],
                                              float rtol, float eps) {
-    cx<T> S[5];
+    cxf S[5];
     float K2[5];
 #pragma unroll
-    for (int i = 0; i < 5; i++) { S[i] = {T(0), T(0)}; K2[i] = 0.f; }
+    for (int i = 0; i < 5; i++) { S[i] = {0.f, 0.f}; K2[i] = 0.f; }
 #pragma unroll
     for (int i = 0; i < 5; i++)
 #pragma unroll
         for (int j = i + 1; j < 5; j++) {
-            float rr;
-            const cx<T> r = pair_inv(z[i] - z[j], rr);
+            const cxf r = inv(diff_f(z[i], z[j]));
             S[i] = S[i] + r;
             S[j] = S[j] - r;
+            const float rr = norm2(r);
             K2[i] += rr;
             K2[j] += rr;
         }
@@ -156,7 +156,7 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
     for (int i = 0; i < 5; i++) {
         cx<T> p, d;
         horner(c, z[i], p, d);
-        w[i] = cdiv(p, d - p * S[i]);
+        w[i] = cdiv(p, d - p * widen(S[i], p));
         const float az = sqrtf(norm2f(z[i]));
         const float dabs = sqrtf(norm2f(d));
         dpa[i] = dabs;
