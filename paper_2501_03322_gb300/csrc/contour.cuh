@@ -160,6 +160,12 @@ __device__ __forceinline__ int link_class(const cxd *X, const cxd *Y, int x0, in
     constexpr int N = NX > NY ? NX : NY;
     constexpr int M = NX > NY ? NY : NX;
     constexpr int NP = N == 1 ? 1 : (N == 2 ? 2 : 6);
+    // each distance once (the permutations share them)
+    float dist[NX][NY];
+#pragma unroll
+    for (int a = 0; a < NX; a++)
+#pragma unroll
+        for (int b = 0; b < NY; b++) dist[a][b] = sqrtf(norm2(to_f(Y[y0 + b] - X[x0 + a])));
     float best_cost = 3.0e38f;
     int best = 0;
 #pragma unroll
@@ -168,8 +174,7 @@ __device__ __forceinline__ int link_class(const cxd *X, const cxd *Y, int x0, in
 #pragma unroll
         for (int i = 0; i < M; i++) {
             const int j = perm_at<N>(p, i);
-            const cxf d = to_f((NX <= NY) ? (Y[y0 + j] - X[x0 + i]) : (Y[y0 + i] - X[x0 + j]));
-            cost += sqrtf(norm2(d));
+            cost += (NX <= NY) ? dist[i][j] : dist[j][i];
         }
         if (cost < best_cost) { best_cost = cost; best = p; }
     }

@@ -301,6 +301,7 @@ __device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, 
     cxf f1f[5], d1f[5], d2f[5];
     float ca[6];
     abs_coeffs(c, ca);
+    const float m1f = (float)L.m1, m2f = (float)L.m2;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         const cxd d1 = inv(cxd{z[i].x + L.s, z[i].y}); // 1/(eta + s) = -1/(z1 - z)
@@ -308,14 +309,23 @@ __device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, 
         const cxd g = L.m1 * d1 + L.m2 * d2;           // = -f(z)
         R[i] = y - z[i] + conj(g);                     // Eq. 12
         aR[i] = (float)norm2(R[i]);
-        const cxd d1s = d1 * d1, d2s = d2 * d2;
-        const cxd f1 = L.m1 * d1s + L.m2 * d2s;        // f'(z)
-        const double J = 1.0 - norm2(f1);              // Eq. 7
-        Jpos[i] = J > 0.0;
-        Jf[i] = (float)J;
-        f1f[i] = to_f(f1);
         d1f[i] = to_f(d1);
         d2f[i] = to_f(d2);
+        // f'(z) and J (Eq. 7) in FP32, redone in FP64 next to a critical
+        // curve (|J| < 1e-2), where the parity sign and 1/J need it
+        cxf f1 = m1f * (d1f[i] * d1f[i]) + m2f * (d2f[i] * d2f[i]);
+        float J = 1.0f - norm2(f1);
+        bool pos = J > 0.0f;
+        if (fabsf(J) < 1e-2f) {
+            const cxd f1d = L.m1 * (d1 * d1) + L.m2 * (d2 * d2);
+            const double Jd = 1.0 - norm2(f1d);
+            pos = Jd > 0.0;
+            J = (float)Jd;
+            f1 = to_f(f1d);
+        }
+        Jpos[i] = pos;
+        Jf[i] = J;
+        f1f[i] = f1;
         const float az = sqrtf(norm2f(z[i]));
         noise[i] = 1.1e-16f * horner_bound(ca, az) * (1.0f + fabsf(f1f[i].x) + fabsf(f1f[i].y)) / fmaxf(dpa[i], 1e-37f);
     }
@@ -356,7 +366,6 @@ __device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, 
     // derivatives (Eq. 10, with conj(f') in dz/dtheta) and storage
     const cxf dzf = to_f(dzeta);
     const float rho2 = (float)(L.rho * L.rho);
-    const float m1f = (float)L.m1, m2f = (float)L.m2;
     uint32_t meta = (uint32_t)count;
     int kp = 0, kn = (count - 1) / 2;
 #pragma unroll
