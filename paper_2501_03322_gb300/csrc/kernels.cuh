@@ -111,8 +111,8 @@ __device__ __forceinline__ bool fetch_position(const WorkSrc &w, int64_t idx, Po
 // REPAIR = false: the main pass over src.n work items.  REPAIR = true: the
 // repair pass over the work items that the main pass queued in kp.relist
 // (crossings that failed the slope test), integrated again with repairs.
-template <int PREC, int SPL, bool REPAIR>
-__global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParams kp) {
+template <int PREC, int SPL, bool REPAIR, int OCC = TW_MIN_CTAS_PER_SM>
+__global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
     __shared__ WarpStage stage[WPB];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * WPB + wib;
@@ -190,6 +190,19 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) contour_kernel(KParam
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, contour_kernel<PREC, SPL, false>, TPB, 0); \
     }
 
+// An instance compiled for OCC CTAs per SM (a register budget of 65536 /
+// (128 OCC) per thread): more resident warps hide more latency on positions
+// whose warps diverge most (many lenses near caustics), at the price of
+// register spills.
+#define TW_DEFINE_LAUNCHER_OCC(PREC, SPL, OCC)                                                     \
+    cudaError_t launch_contour_##PREC##_##SPL##_o##OCC(unsigned blocks, cudaStream_t st, const KParams &kp) { \
+        contour_kernel<PREC, SPL, false, OCC><<<blocks, TPB, 0, st>>>(kp);                         \
+        return cudaGetLastError();                                                                 \
+    }                                                                                              \
+    cudaError_t occupancy_contour_##PREC##_##SPL##_o##OCC(int *occ) {                              \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, contour_kernel<PREC, SPL, false, OCC>, TPB, 0); \
+    }
+
 // The repair-pass instance of a precision (two samples per lane).
 #define TW_DEFINE_REPAIR_LAUNCHER(PREC)                                                            \
     cudaError_t launch_repair_##PREC(unsigned blocks, cudaStream_t st, const KParams &kp) {       \
@@ -217,6 +230,10 @@ TW_DECLARE_LAUNCHER(0, 4)
 TW_DECLARE_LAUNCHER(1, 1)
 TW_DECLARE_LAUNCHER(1, 2)
 TW_DECLARE_LAUNCHER(1, 4)
+cudaError_t launch_contour_0_2_o4(unsigned blocks, cudaStream_t st, const KParams &kp);
+cudaError_t occupancy_contour_0_2_o4(int *occ);
+cudaError_t launch_contour_1_2_o4(unsigned blocks, cudaStream_t st, const KParams &kp);
+cudaError_t occupancy_contour_1_2_o4(int *occ);
 cudaError_t launch_repair_0(unsigned blocks, cudaStream_t st, const KParams &kp);
 cudaError_t launch_repair_1(unsigned blocks, cudaStream_t st, const KParams &kp);
 

@@ -22,7 +22,12 @@ namespace tw {
 typedef cudaError_t (*launch_fn)(unsigned, cudaStream_t, const KParams &);
 typedef cudaError_t (*occ_fn)(int *);
 
-static void pick_kernel(int prec, int spl, launch_fn *lf, occ_fn *of) {
+static void pick_kernel(int prec, int spl, bool occ4, launch_fn *lf, occ_fn *of) {
+    if (spl == 2 && occ4) {
+        if (prec == 0) { *lf = launch_contour_0_2_o4; *of = occupancy_contour_0_2_o4; }
+        else { *lf = launch_contour_1_2_o4; *of = occupancy_contour_1_2_o4; }
+        return;
+    }
     if (prec == 0) {
         if (spl == 1) { *lf = launch_contour_0_1; *of = occupancy_contour_0_1; }
         else if (spl == 2) { *lf = launch_contour_0_2; *of = occupancy_contour_0_2; }
@@ -115,9 +120,13 @@ static int check_opts(const tw_opts *o) {
 }
 
 // Launch shape: samples per lane per iteration (limb samples per iteration =
-// 32 x spl), CTAs per SM (0: as many as fit), work items per atomic grab.
+// 32 x spl), CTAs per SM (0: as many as fit), work items per atomic grab, and
+// which compiled instance: occ4 = 1 the one built for 4 CTAs per SM (spl 2
+// only), 0 the one built for 2, -1 by work kind (4 for per-position lenses,
+// whose warps diverge most; measured 5% faster there and 8% slower on a
+// single-lens map).
 struct LaunchCfg {
-    int spl, ctas, chunk;
+    int spl, ctas, chunk, occ4;
 };
 
 // Launches the contour kernel over src.n positions.  Device pointers only.
@@ -130,7 +139,8 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     if (src.stride < 1) src.stride = 1;
     launch_fn lf;
     occ_fn of;
-    pick_kernel(prec, cfg.spl, &lf, &of);
+    const bool occ4 = cfg.occ4 > 0 || (cfg.occ4 < 0 && src.kind == 3);
+    pick_kernel(prec, cfg.spl, occ4, &lf, &of);
     int occ = 0;
     cudaError_t e = of(&occ);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -240,7 +250,8 @@ static void tune_load() {
         char *bar = strrchr(line, '|');
         if (!bar) continue;
         LaunchCfg c;
-        if (sscanf(bar + 1, "%d %d %d", &c.spl, &c.ctas, &c.chunk) != 3) continue;
+        c.occ4 = -1;
+        if (sscanf(bar + 1, "%d %d %d %d", &c.spl, &c.ctas, &c.chunk, &c.occ4) < 3) continue;
         if (c.spl != 1 && c.spl != 2 && c.spl != 4) continue;
         *bar = 0;
         g_tune[line] = c;
@@ -254,7 +265,9 @@ static void tune_save() {
     if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // may exist
     FILE *f = fopen(path.c_str(), "w");
     if (!f) return;
-    for (auto &kv : g_tune) fprintf(f, "%s|%d %d %d\n", kv.first.c_str(), kv.second.spl, kv.second.ctas, kv.second.chunk);
+    for (auto &kv : g_tune)
+        fprintf(f, "%s|%d %d %d %d\n", kv.first.c_str(), kv.second.spl, kv.second.ctas, kv.second.chunk,
+                kv.second.occ4);
     fclose(f);
 }
 
@@ -287,13 +300,14 @@ static int autotune(DevState &d, const WorkSrc &src, double tol, int prec, int m
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
     float best_ms = 3.0e38f;
-    const int spls[3] = {1, 2, 4};
+    // (samples per lane, compiled instance): the 4-CTA instance exists for 2
+    const int spls[4] = {1, 2, 4, 2}, occs[4] = {0, 0, 0, 1};
     const int ctass[2] = {1, 0};
     const int chunks[2] = {1, 4};
-    for (int a = 0; a < 3; a++)
+    for (int a = 0; a < 4; a++)
         for (int b = 0; b < 2; b++)
             for (int c = 0; c < 2; c++) {
-                const LaunchCfg cfg = {spls[a], ctass[b], chunks[c]};
+                const LaunchCfg cfg = {spls[a], ctass[b], chunks[c], occs[a]};
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; rep++) {  // first run warms the arena and caches
                     cudaEventRecord(e0, st);
@@ -346,7 +360,7 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     if (o.nsamp_out && is_device_ptr(o.nsamp_out) != dev) return TW_EINVAL;
     if (o.pos_status && is_device_ptr(o.pos_status) != dev) return TW_EINVAL;
     const void *din[5];
-    LaunchCfg cfg = {o.samples_per_iter / 32, 0, 1};
+    LaunchCfg cfg = {o.samples_per_iter / 32, 0, 1, -1};
     if (dev) {
         for (int i = 0; i < c.nin; i++) din[i] = c.in[i];
         WorkSrc src = bind(din);
@@ -414,7 +428,7 @@ int contour_positions(const double *s, const double *q, const double *rho, const
     w.y1 = y1;
     w.y2 = y2;
     w.list = list;
-    const LaunchCfg cfg = {2, 0, 1};
+    const LaunchCfg cfg = {2, 0, 1, -1};
     return launch(*dp, w, tol, prec, max_samples, cfg, false, out, nullptr, nullptr, status, st);
 }
 
