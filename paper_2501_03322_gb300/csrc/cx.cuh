@@ -28,6 +28,14 @@ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
 }
 template <typename T>
 __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.x, s * a.y}; }
+// a b + c as four fused multiply-adds (the operator form leaves a separate
+// multiply and add per component)
+__device__ __forceinline__ cx<double> cmad(cx<double> a, cx<double> b, cx<double> c) {
+    return {fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
+}
+__device__ __forceinline__ cx<float> cmad(cx<float> a, cx<float> b, cx<float> c) {
+    return {fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y))};
+}
 template <typename T>
 __device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.x, -a.y}; }
 template <typename T>

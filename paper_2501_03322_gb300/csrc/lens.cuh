@@ -104,8 +104,8 @@ __device__ __forceinline__ void horner(const cx<T> c[6], cx<T> z, cx<T> &p, cx<T
     d = {T(0), T(0)};
 #pragma unroll
     for (int k = 4; k >= 0; k--) {
-        d = d * z + p;
-        p = p * z + c[k];
+        d = cmad(d, z, p);
+        p = cmad(p, z, c[k]);
     }
 }
 
@@ -156,7 +156,7 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
     for (int i = 0; i < 5; i++) {
         cx<T> p, d;
         horner(c, z[i], p, d);
-        w[i] = cdiv(p, d - p * widen(S[i], p));
+        w[i] = cdiv(p, cmad(cx<T>{-p.x, -p.y}, widen(S[i], p), d));  // p' - p S
         const float az = sqrtf(norm2f(z[i]));
         const float dabs = sqrtf(norm2f(d));
         dpa[i] = dabs;
