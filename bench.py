@@ -38,18 +38,26 @@ sys.path.insert(0, ROOT)
 
 # ---------------------------------------------------------------- FLOP model
 # Algorithmic FLOPs of the method per unit of work counted by the kernel
-# (tw_last_launch_work).  Counting rules: real add/mul 1, complex add 2,
-# complex mul 6, complex multiply-add 8, reciprocal/division/sqrt 1.
-#   one Aberth sweep (five roots): per root Horner p and p' (5 x 16), p/p' (12),
-#     sum of four reciprocal differences (38), correction (22): 152 -> 760
+# (tw_last_launch_work), split by the precision each part runs in.  Counting
+# rules: real add/mul 1, complex add 2, complex mul 6, complex multiply-add 8,
+# reciprocal/division/square root 1.
+#   one Aberth sweep (five roots), FP64 mode: Horner p and p' (5 x 80), the
+#     denominator p' - p S (5 x 8), the division (5 x 12) and the update
+#     (5 x 2) in FP64: 510; the ten pair reciprocals 1/(z_i - z_j), their sums
+#     and the convergence magnitudes in FP32: 225
+#   one Aberth sweep in FP32 (mixed mode): all of it, 760
 #   one limb sample outside the sweeps: limb point (8), Eq. 6 coefficients
-#     (~100), residual/Jacobian/f'/f'' per root (68 -> 340), dz/dtheta and
-#     z' ^ z'' per root (29 -> 145): ~600 (FP64)
+#     (~100) and per root the two lens reciprocals, f(z) and the residual R
+#     (5 x 23) in FP64: ~225; f', J, dz/dtheta, f'' and z' ^ z'' in FP32
+#     (5 x 45): 225
 #   one FP64 Newton pass over the five roots (mixed mode): 5 x 94 = 470
 #   one edge: image linking distances and 3-5 links of trapezium + parabolic
 #     correction + four error terms: ~145 (FP64), ~20 (FP32)
-F_SWEEP = 760.0
-F_SAMPLE64 = 600.0
+F_SWEEP64 = 510.0
+F_SWEEP64_FP32 = 225.0
+F_SWEEP32 = 760.0
+F_SAMPLE64 = 225.0
+F_SAMPLE32 = 225.0
 F_NEWTON64 = 470.0
 F_EDGE64 = 145.0
 F_EDGE32 = 20.0
@@ -179,9 +187,10 @@ class ClockSampler:
 
 
 def flops_of(work, mode):
-    f64 = (F_SAMPLE64 * work["samples"] + F_SWEEP * work["sweeps64"] + F_EDGE64 * work["edges"]
+    f64 = (F_SAMPLE64 * work["samples"] + F_SWEEP64 * work["sweeps64"] + F_EDGE64 * work["edges"]
            + F_NEWTON64 * work["newton64"])
-    f32 = F_SWEEP * work["sweeps32"] + F_EDGE32 * work["edges"]
+    f32 = (F_SAMPLE32 * work["samples"] + F_SWEEP64_FP32 * work["sweeps64"] + F_SWEEP32 * work["sweeps32"]
+           + F_EDGE32 * work["edges"])
     return f64, f32
 
 

@@ -233,11 +233,13 @@ int tw_last_launch_work(int64_t out[5]);
  * counterpart in the paper (a measurement hook of this library). */
 int tw_last_launch_ms(float *ms);
 
-/* Device self-test of the library's FP64 reciprocal (the hardware
- * approximation refined by two Newton-Raphson steps, used for every complex
- * division of the kernels) against IEEE division, over 2^20 values of
- * magnitude 1e-300..1e300: *rcp_max_rel_err receives the largest relative
- * difference.  Synchronous.  The paper has no counterpart. */
+/* Device self-test of the library's FP64 reciprocals against IEEE division,
+ * over 2^20 values of magnitude 1e-300..1e300: rcp_max_rel_err[0] receives the
+ * largest relative difference of the full reciprocal (the hardware
+ * approximation refined by two Newton-Raphson steps, used for the residuals,
+ * the areas and every other FP64 division), rcp_max_rel_err[1] that of the
+ * one-step reciprocal used for the Aberth correction (about 40 bits).
+ * Synchronous.  The paper has no counterpart. */
 int tw_selftest(double *rcp_max_rel_err);
 
 /* Device self-test of the slope test and its repair (Sec. 2.4.2) on a planted

@@ -249,11 +249,11 @@ def surrogate_mag(path, s, q, rho, y1, y2, rel_tol=1e-4, kappa=3.0, precision=PR
     return out, int(c[0])
 
 
-def selftest_rcp() -> float:
-    """Largest relative error of the device FP64 reciprocal against IEEE division."""
-    v = ctypes.c_double(0.0)
-    _check(lib().tw_selftest(ctypes.byref(v)))
-    return v.value
+def selftest_rcp() -> tuple:
+    """Largest relative errors of the device FP64 reciprocals (full, one-step) against IEEE division."""
+    v = np.zeros(2)
+    _check(lib().tw_selftest(v.ctypes.data_as(ctypes.c_void_p)))
+    return float(v[0]), float(v[1])
 
 
 def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64, max_samples=4096,

@@ -60,6 +60,23 @@ __device__ __forceinline__ double rcp(double v) {
     e = fma(-v, y, 1.0);
     return fma(y, e, y);
 }
+// FP64 reciprocal to about 40 bits (the approximation and one refinement
+// step): for quantities whose relative accuracy need not reach FP64, such as
+// the Aberth correction of a root (its error then scales the correction,
+// which vanishes at convergence).
+__device__ __forceinline__ double rcp40(double v) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(v));
+    const double e = fma(-v, y, 1.0);
+    return fma(y, e, y);
+}
+// a / b with rcp40.
+__device__ __forceinline__ cx<double> cdiv40(cx<double> a, cx<double> b) {
+    const double r = rcp40(fmax(norm2(b), 1e-300));
+    return {(a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r};
+}
+__device__ __forceinline__ cx<float> cdiv40(cx<float> a, cx<float> b);
+
 // FP32 reciprocal: the hardware approximation (rcp.approx.ftz.f32, ~1 ulp),
 // enough for the FP32 root iteration.
 __device__ __forceinline__ float rcp(float v) {
@@ -91,6 +108,8 @@ __device__ __forceinline__ cxf cdiv(cxf a, cxf b) {
     float r = rcp(norm2(bb));
     return {(aa.x * bb.x + aa.y * bb.y) * r, (aa.y * bb.x - aa.x * bb.y) * r};
 }
+
+__device__ __forceinline__ cxf cdiv40(cxf a, cxf b) { return cdiv(a, b); }
 
 __device__ __forceinline__ cxf to_f(cxd a) { return {(float)a.x, (float)a.y}; }
 __device__ __forceinline__ cxd to_d(cxf a) { return {(double)a.x, (double)a.y}; }

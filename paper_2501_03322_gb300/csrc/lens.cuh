@@ -124,7 +124,8 @@ __device__ __forceinline__ cxf widen(cxf s, cxf) { return s; }
 // which vanishes at a root, so their rounding changes the correction w_i by a
 // relative amount of order eps32 |w_i| |S_i| and limits neither the
 // convergence nor the attainable accuracy (set by p, p' and z in the
-// iterate's type).
+// iterate's type).  For the same reason the division takes a reciprocal good
+// to about 40 bits.
 // dpa[i] receives |p'(z_i)|.  Returns true when every root is converged: its
 // correction, or the error left after it, is below
 // thr_i = max(rtol |z_i|, 8 eps B_i/|p'(z_i)|) (B_i the Horner round-off
@@ -156,7 +157,7 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
     for (int i = 0; i < 5; i++) {
         cx<T> p, d;
         horner(c, z[i], p, d);
-        w[i] = cdiv(p, cmad(cx<T>{-p.x, -p.y}, widen(S[i], p), d));  // p' - p S
+        w[i] = cdiv40(p, cmad(cx<T>{-p.x, -p.y}, widen(S[i], p), d));  // p / (p' - p S)
         const float az = sqrtf(norm2f(z[i]));
         const float dabs = sqrtf(norm2f(d));
         dpa[i] = dabs;

@@ -575,14 +575,14 @@ int tw_selftest(double *rcp_max_rel_err) {
     DevState *dp = nullptr;
     int rc = dev_state(&dp);
     if (rc) return rc;
-    unsigned long long *slot = dp->counter + 6;  // scratch word of the control block
+    unsigned long long *slot = dp->counter + 6;  // two scratch words of the control block
     cudaError_t e = cudaStreamWaitEvent(0, dp->last, 0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(slot, 0, 8, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(slot, 0, 16, 0);
     if (e == cudaSuccess) e = launch_rcp_selftest(slot, 1 << 20, 0);
-    unsigned long long h = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&h, slot, 8, cudaMemcpyDeviceToHost);
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, slot, 16, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e);
-    memcpy(rcp_max_rel_err, &h, 8);
+    memcpy(rcp_max_rel_err, h, 16);
     return TW_OK;
 }
 
