@@ -100,10 +100,10 @@ __device__ __forceinline__ float horner_bound(const float ca[6], float az) {
 // p(z) and p'(z) by Horner's rule.
 template <typename T>
 __device__ __forceinline__ void horner(const cx<T> c[6], cx<T> z, cx<T> &p, cx<T> &d) {
-    p = c[5];
-    d = {T(0), T(0)};
+    d = c[5];
+    p = cmad(c[5], z, c[4]);
 #pragma unroll
-    for (int k = 4; k >= 0; k--) {
+    for (int k = 3; k >= 0; k--) {
         d = cmad(d, z, p);
         p = cmad(p, z, c[k]);
     }
@@ -133,9 +133,14 @@ __device__ __forceinline__ cxf widen(cxf s, cxf) { return s; }
 // The iteration converges cubically, the error after a step being about
 // |w_i|^2 max_j|w_j| sum_j 1/|z_i - z_j|^2, so a sweep whose corrections are
 // already small needs no confirming sweep.
+// thr[] and az2[] (|z_i|^2) carry the thresholds between sweeps: with fresh
+// = true they (and dpa) are computed from this sweep's z and p', otherwise
+// the previous values are kept (the magnitudes cost FP64-pipe conversions).
+// fresh is set on return when some root moved by more than 1e-3 |z_i|, i.e.
+// when the magnitudes may have changed.
 template <typename T>
 __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6], cx<T> z[5], float dpa[5],
-                                             float rtol, float eps) {
+                                             float rtol, float eps, float thr[5], float az2[5], bool &fresh) {
     cxf S[5];
     float K2[5];
 #pragma unroll
@@ -152,19 +157,26 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
             K2[j] += rr;
         }
     cx<T> w[5];
-    float wa2[5], thr[5], wmax = 0.f;
+    float wa2[5], wmax = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         cx<T> p, d;
         horner(c, z[i], p, d);
         w[i] = cdiv40(p, cmad(cx<T>{-p.x, -p.y}, widen(S[i], p), d));  // p / (p' - p S)
-        const float az = sqrtf(norm2f(z[i]));
-        const float dabs = sqrtf(norm2f(d));
-        dpa[i] = dabs;
-        thr[i] = fmaxf(rtol * az, 8.0f * eps * horner_bound(ca, az) / fmaxf(dabs, 1e-37f));
+        if (fresh) {
+            az2[i] = norm2f(z[i]);
+            const float az = sqrtf(az2[i]);
+            const float dabs = sqrtf(norm2f(d));
+            dpa[i] = dabs;
+            thr[i] = fmaxf(rtol * az, 8.0f * eps * horner_bound(ca, az) / fmaxf(dabs, 1e-37f));
+        }
         wa2[i] = norm2f(w[i]);
         wmax = fmaxf(wmax, wa2[i]);
     }
+    bool moved = false;
+#pragma unroll
+    for (int i = 0; i < 5; i++) moved = moved || !(wa2[i] <= 1e-6f * az2[i]);
+    fresh = moved;
     wmax = sqrtf(wmax);
     bool conv = true;
 #pragma unroll
@@ -174,6 +186,15 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
         conv = conv && (wa2[i] <= thr[i] * thr[i] || after <= 0.25f * thr[i]);
     }
     return conv;
+}
+
+// One sweep with freshly computed thresholds.
+template <typename T>
+__device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6], cx<T> z[5], float dpa[5],
+                                             float rtol, float eps) {
+    float thr[5], az2[5];
+    bool fresh = true;
+    return aberth_sweep<T>(c, ca, z, dpa, rtol, eps, thr, az2, fresh);
 }
 
 // Aberth starting points on a circle enclosing the roots (cold start).
@@ -269,9 +290,11 @@ __device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa
 #pragma unroll
         for (int i = 0; i < 5; i++) z[i] = to_d(zf[i]);
     }
+    float thr[5], az2[5];
+    bool fresh = true;
     for (int it = 0; it < maxit; it++) {
         sw64++;
-        if (aberth_sweep<double>(c, ca, z, dpa, 1e-14f, 1.1e-16f)) return 0;
+        if (aberth_sweep<double>(c, ca, z, dpa, 1e-14f, 1.1e-16f, thr, az2, fresh)) return 0;
     }
     return SF_SOLVER;
 }
