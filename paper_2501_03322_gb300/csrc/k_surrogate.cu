@@ -168,7 +168,7 @@ __global__ void sur_sample_kernel(uint64_t seed, int64_t n, double *S, double *Q
 
 // ------------------------------------------------ point-source images, flag
 // Images of a point source at y (secondary frame): FP32 Aberth from z, then
-// (fp64 = true) two FP64 Newton steps.  Returns the image count by the
+// (fp64 = true) one or two FP64 Newton steps.  Returns the image count by the
 // residual pair test (Sec. 2.4.1) and, for the real images, sum 1/|J| and
 // min |J| (Eq. 7).
 template <bool FP64>
@@ -196,11 +196,17 @@ static __device__ __noinline__ int point_images(const LensK &L, cxd y, cxd z[5],
     for (int i = 0; i < 5; i++) {
         z[i] = to_d(zf[i]);
         if (FP64) {
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                cxd p, d;
+            // one Newton step from FP32 accuracy reaches FP64 accuracy (the error
+            // squares); a second where the FP32 root was poor (a step above
+            // 1e-6 |z|, next to a near-double root)
+            cxd p, d;
+            horner(c, z[i], p, d);
+            cxd st = cdiv40(p, d);
+            z[i] = z[i] - st;
+            if (norm2f(st) > 1e-12f * norm2f(z[i])) {
                 horner(c, z[i], p, d);
-                z[i] = z[i] - cdiv(p, d);
+                st = cdiv40(p, d);
+                z[i] = z[i] - st;
             }
         }
     }
@@ -324,36 +330,65 @@ __device__ bool caustic_within(float s, float m2, float m1, cxf y0, float reach)
 }
 
 // Raw features, point-source magnification and near-caustic flag per query.
-__global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const double *S, const double *Q, const double *RHO, const double *Y1,
-                                    const double *Y2, float *X, double *MUPS, uint8_t *FLAG, float *HEXE) {
+// One thread per query for its centre solve and caustic sweep; the 24 ring
+// points of the queries of a warp that are still unflagged are then spread
+// over all 32 lanes (lanes whose queries were flagged would otherwise idle),
+// each lane taking the lens and centre images of the query it serves by warp
+// shuffles, and each query's owner sums its ring values in a fixed order.
+constexpr int RING_PTS = 24;  // 3 rings x 8 points
+
+__global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const double *S, const double *Q,
+                                                              const double *RHO, const double *Y1, const double *Y2,
+                                                              float *X, double *MUPS, uint8_t *FLAG, float *HEXE) {
+    __shared__ double sM[4][32][RING_PTS];  // ring-point magnifications per query slot
+    __shared__ int sBad[4][32];             // a ring point's image count differed
+    __shared__ int sOwner[4][32];           // lane of the j-th unflagged query
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = S[i], q = Q[i], rho = RHO[i], y1 = Y1[i], y2 = Y2[i];
-    float *x = X + i * SXP;
-    x[0] = (float)log10(s);
-    x[1] = (float)log10(q);
-    x[2] = (float)log10(rho);
-    x[3] = (float)y1;
-    x[4] = (float)y2;
-    x[5] = x[6] = x[7] = 0.f;
-    const bool ok = s > 0 && q > 0 && rho > 0 && isfinite(s) && isfinite(q) && isfinite(rho) && isfinite(y1) &&
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const bool in = i < n;
+    double s = 1.0, q = 1.0, rho = 1.0, y1 = 0.0, y2 = 0.0;
+    if (in) {
+        s = S[i];
+        q = Q[i];
+        rho = RHO[i];
+        y1 = Y1[i];
+        y2 = Y2[i];
+        float *x = X + i * SXP;
+        x[0] = (float)log10(s);
+        x[1] = (float)log10(q);
+        x[2] = (float)log10(rho);
+        x[3] = (float)y1;
+        x[4] = (float)y2;
+        x[5] = x[6] = x[7] = 0.f;
+    }
+    const bool ok = in && s > 0 && q > 0 && rho > 0 && isfinite(s) && isfinite(q) && isfinite(rho) && isfinite(y1) &&
                     isfinite(y2);
-    if (!ok) { MUPS[i] = __longlong_as_double(0x7ff8000000000000ll); FLAG[i] = 1; HEXE[i] = 1.f; return; }
-    if (q > 1.0) { q = 1.0 / q; y1 = -y1; }  // mass-swap symmetry (see kernels.cuh)
     LensK L;
-    L.s = s;
-    L.m1 = 1.0 / (1.0 + q);
-    L.m2 = q * L.m1;
-    L.rho = rho;
-    const cxd y0 = {y1 - s * L.m1, y2};
+    L.s = 1.0;
+    L.m1 = 1.0;
+    L.m2 = 0.0;
+    L.rho = 1.0;
+    cxd y0 = {0.0, 0.0};
     cxd z[5];
-    initial_roots(s, y0, z);
-    double A0, minJ;
-    const int c0 = point_images<true>(L, y0, z, A0, minJ);
-    bool flag = !(isfinite(A0) && A0 >= 1.0 - 1e-3) || minJ < 0.1;
-    // within 4 rho (not just 2 rho): closer than that the ring at 2 rho nears
-    // the caustic and the expansion's error estimate is no longer reliable
-    if (!flag) flag = caustic_within((float)s, (float)L.m2, (float)L.m1, to_f(y0), (float)(4.0 * rho) + 1e-6f);
+#pragma unroll
+    for (int k = 0; k < 5; k++) z[k] = {0.0, 0.0};
+    double A0 = __longlong_as_double(0x7ff8000000000000ll), minJ = 0.0;
+    int c0 = 0;
+    bool flag = true;
+    if (ok) {
+        if (q > 1.0) { q = 1.0 / q; y1 = -y1; }  // mass-swap symmetry (see kernels.cuh)
+        L.s = s;
+        L.m1 = 1.0 / (1.0 + q);
+        L.m2 = q * L.m1;
+        L.rho = rho;
+        y0 = {y1 - s * L.m1, y2};
+        initial_roots(s, y0, z);
+        c0 = point_images<true>(L, y0, z, A0, minJ);
+        flag = !(isfinite(A0) && A0 >= 1.0 - 1e-3) || minJ < 0.1;
+        // within 4 rho (not just 2 rho): closer than that the ring at 2 rho nears
+        // the caustic and the expansion's error estimate is no longer reliable
+        if (!flag) flag = caustic_within((float)s, (float)L.m2, (float)L.m1, to_f(y0), (float)(4.0 * rho) + 1e-6f);
+    }
     // Point-source magnifications averaged over 8 points on rings of radius
     // rho/2, rho and 2 rho.  For a smooth A, the average over a ring of radius
     // r is A0 + c1 r^2 + c2 r^4 + c3 r^6 + ... (c1 = lap A / 4, c2 = lap^2 A / 64)
@@ -365,35 +400,65 @@ __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const d
     // difference of the two, 15/24 c3 rho^6 (about 15 times its error while
     // the series converges), is its error estimate.  The image count must be
     // the centre's at every ring point (otherwise a caustic is within 2 rho).
-    double R[3] = {0.0, 0.0, 0.0};
-    for (int ring = 0; ring < 3 && !flag; ring++)
-        for (int k = 0; k < 8 && !flag; k++) {
+    const bool want = ok && !flag;
+    const unsigned act = __ballot_sync(0xffffffffu, want);
+    const int na = __popc(act);
+    sBad[wib][lane] = 0;
+    if (want) sOwner[wib][__popc(act & ((1u << lane) - 1u))] = lane;
+    __syncwarp();
+    for (int base = 0; base < RING_PTS * na; base += 32) {
+        const int t = base + lane;
+        const bool has = t < RING_PTS * na;
+        const int j = has ? t / RING_PTS : 0, k = t % RING_PTS;
+        const int src = sOwner[wib][has ? j : 0];
+        LensK Lk;
+        Lk.s = __shfl_sync(0xffffffffu, L.s, src);
+        Lk.m1 = __shfl_sync(0xffffffffu, L.m1, src);
+        Lk.m2 = __shfl_sync(0xffffffffu, L.m2, src);
+        Lk.rho = __shfl_sync(0xffffffffu, L.rho, src);
+        const cxd yc = {__shfl_sync(0xffffffffu, y0.x, src), __shfl_sync(0xffffffffu, y0.y, src)};
+        cxd zk[5];
+#pragma unroll
+        for (int a = 0; a < 5; a++) zk[a] = {__shfl_sync(0xffffffffu, z[a].x, src), __shfl_sync(0xffffffffu, z[a].y, src)};
+        const int ck = __shfl_sync(0xffffffffu, c0, src);
+        if (has) {
+            const int ring = k >> 3;
             double sn, cs;
-            sincos(0.7853981633974483 * k + 0.2, &sn, &cs);
-            const double r = (0.5 * (1 << ring)) * rho;
-            const cxd yk = {y0.x + r * cs, y0.y + r * sn};
-            cxd zk[5] = {z[0], z[1], z[2], z[3], z[4]};
+            sincos(0.7853981633974483 * (k & 7) + 0.2, &sn, &cs);
+            const double r = (0.5 * (1 << ring)) * Lk.rho;
+            const cxd yk = {yc.x + r * cs, yc.y + r * sn};
             double m, mj;
-            if (point_images<true>(L, yk, zk, m, mj) != c0 || !isfinite(m)) flag = true;
-            R[ring] += 0.125 * m;
+            const int cnt = point_images<true>(Lk, yk, zk, m, mj);
+            sM[wib][src][k] = m;
+            if (cnt != ck || !isfinite(m)) atomicOr(&sBad[wib][src], 1);
         }
-    double Ahex = A0, hexe = 1.0;
-    if (!flag) {
-        // disc average from the rings at lam rho and 2 lam rho
-        auto disc = [A0](double Ra, double Rb, double lam) {
-            const double d1 = Ra - A0, d2 = Rb - A0, l2 = lam * lam;
-            const double c2 = (d2 - 4.0 * d1) / (12.0 * l2 * l2);  // c2 rho^4
-            const double c1 = d1 / l2 - c2 * l2;                   // c1 rho^2
-            return A0 + 0.5 * c1 + c2 / 3.0;
-        };
-        Ahex = disc(R[0], R[1], 0.5);
-        hexe = fabs(disc(R[1], R[2], 1.0) - Ahex) / Ahex;
-        // a series that is not converging marks the neighbourhood of a caustic
-        if (!(Ahex > 0.0) || !(hexe <= 0.05)) flag = true;
     }
-    MUPS[i] = Ahex;
-    FLAG[i] = flag ? 1 : 0;
-    HEXE[i] = (float)fmin(hexe, 1.0);
+    __syncwarp();
+    double Ahex = A0, hexe = 1.0;
+    if (want) {
+        double R[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < RING_PTS; k++) R[k >> 3] += 0.125 * sM[wib][lane][k];
+        if (sBad[wib][lane]) flag = true;
+        if (!flag) {
+            // disc average from the rings at lam rho and 2 lam rho
+            auto disc = [A0](double Ra, double Rb, double lam) {
+                const double d1 = Ra - A0, d2 = Rb - A0, l2 = lam * lam;
+                const double c2 = (d2 - 4.0 * d1) / (12.0 * l2 * l2);  // c2 rho^4
+                const double c1 = d1 / l2 - c2 * l2;                   // c1 rho^2
+                return A0 + 0.5 * c1 + c2 / 3.0;
+            };
+            Ahex = disc(R[0], R[1], 0.5);
+            hexe = fabs(disc(R[1], R[2], 1.0) - Ahex) / Ahex;
+            // a series that is not converging marks the neighbourhood of a caustic
+            if (!(Ahex > 0.0) || !(hexe <= 0.05)) flag = true;
+        }
+    }
+    if (in) {
+        MUPS[i] = ok ? Ahex : __longlong_as_double(0x7ff8000000000000ll);
+        FLAG[i] = flag ? 1 : 0;
+        HEXE[i] = (float)fmin(hexe, 1.0);
+    }
 }
 
 // ------------------------------------------------------------- MLP kernels
