@@ -220,7 +220,8 @@ int tw_version(void);
 /* Work done by the most recent launch on the current device (waits for it):
  * out[0] limb samples, out[1] FP64 Aberth sweeps (five roots each), out[2]
  * FP32 Aberth sweeps, out[3] edge evaluations (image linking + area + error),
- * out[4] FP64 Newton passes over the five roots (mixed precision).
+ * out[4] FP64 Newton passes over the five roots (zero: the mixed-precision
+ * polish is counted in out[1] as FP64 Aberth sweeps).
  * These are the units of the FLOP accounting of the roofline report; the
  * paper has no counterpart (it reports no operation counts). */
 int tw_last_launch_work(int64_t out[5]);

@@ -9,19 +9,19 @@
 // Steps, each following the paper:
 //   coefficients   Eq. 6 (cancellation-free form), FP64
 //   roots          Aberth-Ehrlich simultaneous iteration warm-started from a
-//                  neighbouring sample's roots.  FP64 mode iterates in FP64;
-//                  mixed mode iterates in FP32 and then takes one FP64 Newton
-//                  step per root on the undeflated quintic (two where the
-//                  quadratic error bound of the first is not yet at the FP64
-//                  target), falling back to FP64 iteration when a step is not
-//                  well inside the root's basin.  The
+//                  neighbouring sample's roots.  FP64 mode iterates in FP64
+//                  (the pair sums in FP32, see aberth_sweep); mixed mode
+//                  iterates in FP32 to FP32 accuracy and then polishes with
+//                  FP64 sweeps on the undeflated quintic, the first of which
+//                  the cubic convergence estimate almost always accepts.  The
 //                  paper uses the Skowron-Gould Newton/Laguerre solver
 //                  (Sec. 2.2); any solver returning the five roots computes
 //                  the same thing.
 //   ghost test     residual R_i of Eq. 12 in FP64; ghosts are the pair whose
 //                  residuals are equal and opposite (Sec. 2.4.1) and well above
 //                  the round-off level of those roots
-//   parity         sign of J (Eq. 7) in FP64; a sample is accepted when it has
+//   parity         sign of J (Eq. 7), in FP32 away from critical curves and
+//                  FP64 next to them; a sample is accepted when it has
 //                  3 or 5 real images with parity sum -1 (Sec. 2.3)
 //   derivatives    dz/dtheta = (zeta' - conj(f') conj(zeta'))/J and
 //                  z' ^ z'' = (rho^2 + Im(z'^2 zeta' f''))/J  (Eq. 10), in FP32:
@@ -216,8 +216,8 @@ __device__ __forceinline__ bool roots_finite(const cxd z[5]) {
 }
 
 // Roots of the quintic c starting from z (see the header comment).  sw64 and
-// sw32 count FP64 and FP32 Aberth sweeps, nw64 FP64 Newton passes over the
-// five roots.  Returns SF_SOLVER when the iteration limit was reached.
+// sw32 count FP64 and FP32 Aberth sweeps (nw64, FP64 Newton passes, is kept
+// for the work counters and stays zero).  Returns SF_SOLVER when the iteration limit was reached.
 template <int PREC>
 __device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa[5], int maxit, int &sw64, int &sw32,
                                              int &nw64) {
@@ -242,51 +242,9 @@ __device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa
             conv = aberth_sweep<float>(cf, caf, zf, dpa, 2e-6f, 6e-8f);
             sw32++;
         }
-        // FP64 Newton steps per root on the undeflated quintic: the error left
-        // after a step of size st is about |st|^2 sum_j 1/|z_i - z_j|; one step
-        // from FP32 accuracy usually reaches the FP64 target, a second is taken
-        // where it does not.  Every first step must also be well inside the
-        // root's basin (small against the distance to the nearest other root).
-        bool ok = true, need2 = false;
-        float K[5], lim[5];
-#pragma unroll
-        for (int i = 0; i < 5; i++) {
-            float sep2 = 3.0e38f, k = 0.f;
-#pragma unroll
-            for (int j = 0; j < 5; j++)
-                if (j != i) {
-                    const float d2 = fmaxf(norm2(zf[i] - zf[j]), 1e-37f);
-                    sep2 = fminf(sep2, d2);
-                    k += rsqrtf(d2);
-                }
-            K[i] = k;
-            cxd zi = to_d(zf[i]), p, d;
-            horner(c, zi, p, d);
-            const cxd st = cdiv(p, d);
-            z[i] = zi - st;
-            const float az = sqrtf(norm2(zf[i]));
-            const float dabs = sqrtf((float)norm2(d));
-            dpa[i] = dabs;
-            lim[i] = fmaxf(1e-13f * az, 8.0f * 1.1e-16f * horner_bound(ca, az) / fmaxf(dabs, 1e-37f));
-            const float s1 = (float)norm2(st);
-            ok = ok && (s1 <= 2.5e-3f * sep2) && isfinite(s1);
-            need2 = need2 || (s1 * k > lim[i]);
-        }
-        nw64++;
-        if (ok && need2) {
-#pragma unroll
-            for (int i = 0; i < 5; i++) {
-                cxd p, d;
-                horner(c, z[i], p, d);
-                const cxd st = cdiv(p, d);
-                z[i] = z[i] - st;
-                const float s2 = (float)norm2(st);
-                ok = ok && (s2 * K[i] <= lim[i]) && isfinite(s2);
-            }
-            nw64++;
-        }
-        if (ok) return 0;
-        // fallback: FP64 iteration from the FP32 roots
+        // FP64 Aberth sweeps from the FP32 roots: from FP32 accuracy the
+        // cubic convergence estimate usually accepts the first sweep, which
+        // polishes all five roots at once
 #pragma unroll
         for (int i = 0; i < 5; i++) z[i] = to_d(zf[i]);
     }
