@@ -5,8 +5,10 @@ One step = one call of the C ABI over the whole workload (every position
 answered to rel_tol), inputs resident in device memory.  Default workload:
 surrogate + fallback on 1e7 fresh queries near caustics (log10 s ~ U[-0.5,
 0.5], log10 q ~ U[-5, -1], log10 rho ~ U[-4, -2]; network trained once on 1e7
-contour-integrated samples before timing), rel_tol=1e-4, FP64 fallback, with
-the plain contour integration of the same queries timed beside it.  Other
+contour-integrated samples before timing), rel_tol=1e-4, mixed-precision
+fallback (FP32 root iterations, FP64 polish, coefficients, residuals and
+areas), with the plain contour integration of the same queries timed beside
+it.  Other
 workloads: the 512 x 512 planetary-caustic map, the central-caustic light
 curve, 4096 batched light curves, the resonant large source.  Prints one
 JSON line (rank 0).
@@ -300,7 +302,7 @@ def main():
     ap.add_argument("--workload", default="surrogate",
                     choices=["map_planetary", "lightcurve_central", "stress_resonant", "batch_lightcurves",
                              "surrogate"])
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-sample", type=int, default=128, help="positions in the CPU oracle baseline sample")
     ap.add_argument("--ref-sample", type=int, default=24, help="positions per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -79,7 +79,8 @@ enum {
 
 /* Arithmetic modes. */
 enum {
-    TW_PREC_FP64 = 0, /* every step in FP64 */
+    TW_PREC_FP64 = 0, /* root iterations in FP64 (their pair sums in FP32);
+                         coefficients, residuals and area sums in FP64 */
     TW_PREC_MIXED = 1 /* root iterations in FP32, then FP64 polish; coefficients
                          (Eq. 6), residual test (Eq. 12) and area sums in FP64 */
 };

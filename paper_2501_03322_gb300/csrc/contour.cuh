@@ -442,7 +442,7 @@ __device__ __forceinline__ void predict_roots(cxd z[5], const cxf dz[5], unsigne
     }
 }
 
-template <int PREC>
+template <int PREC, bool RP = false>
 static __device__ __noinline__ int limb_sample(const LensK &L, double th, cxd z[5], const Arena &ar, int slot,
                                                WorkCount &wc) {
     double sn, cs;
@@ -453,7 +453,7 @@ static __device__ __noinline__ int limb_sample(const LensK &L, double th, cxd z[
     eq6_coeffs(L.s, L.m2, y, c);
     if (!roots_finite(z)) initial_roots(L.s, y, z);
     float dpa[5];
-    int f = solve_quintic<PREC>(c, z, dpa, 60, wc.sw64, wc.sw32, wc.nw64);
+    int f = solve_quintic<PREC, RP>(c, z, dpa, 60, wc.sw64, wc.sw32, wc.nw64);
     SampleRefs o = {&ar.theta[slot], &ar.roots[slot * 5], &ar.zp[slot * 5], &ar.w[slot * 5], &ar.meta[slot]};
     f |= classify_store(L, y, dzeta, c, z, dpa, th, o);
     return f;
@@ -491,7 +491,7 @@ static __device__ __noinline__ int slope_repairs(const Arena &ar, const uint16_t
 // (the position is then integrated again by the REPAIR = true instance, which
 // repairs such crossings as they appear).  Keeping the repair code out of the
 // main instance keeps its register allocation unchanged.
-template <int PREC, int SPL, bool REPAIR>
+template <int PREC, int SPL, bool REPAIR, bool RP = false>
 __device__ PosResult integrate_position(const LensK &L, double tol, int cap, const Arena &ar, WarpStage &ws) {
     constexpr int SPI = 32 * SPL;
     const int lane = threadIdx.x & 31;
@@ -594,7 +594,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
 #pragma unroll
         for (int i = 0; i < 5; i++) dz[i] = crJ[i] * (dzeta - conj(cf1[i]) * conj(dzeta));
         predict_roots(z, dz, cmask);
-        flags |= limb_sample<PREC>(L, th, z, ar, k, wc);
+        flags |= limb_sample<PREC, RP>(L, th, z, ar, k, wc);
         ar.ordA[k] = (uint16_t)k;
     }
     __syncwarp();
@@ -721,7 +721,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
                     dz[i] = dth * ar.zp[sa * 5 + i];
                 }
                 predict_roots(z, dz, real_mask(ar.meta[sa]));
-                flags |= limb_sample<PREC>(L, tn[t], z, ar, nslot + rk[t], wc);
+                flags |= limb_sample<PREC, RP>(L, tn[t], z, ar, nslot + rk[t], wc);
             }
         // merge into theta order
         for (int p = p0; p < p1; p++) {

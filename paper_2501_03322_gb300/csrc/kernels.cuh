@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
             L.m2 = q * L.m1;
             L.rho = P.rho;
             L.y0 = {y1 - P.s * L.m1, P.y2};  // centre-of-mass -> secondary frame
-            const PosResult r = integrate_position<PREC, SPL, REPAIR>(L, kp.tol, kp.cap, ar, stage[wib]);
+            // the 4-CTA instance serves per-position lenses: its root solver
+            // keeps the pair loop rolled as well (see aberth_sweep)
+            const PosResult r = integrate_position<PREC, SPL, REPAIR, (OCC >= 4)>(L, kp.tol, kp.cap, ar, stage[wib]);
             // a crossing failed the slope test: queue the position for the
             // repair pass (its outputs below are overwritten there)
             if (!REPAIR && (r.status & PS_SLOPE) && kp.relist && lane == 0) {
