@@ -186,10 +186,11 @@ int tw_surrogate_train(const char *weights_path, int64_t nsamples, uint64_t seed
  * is not flagged as near a caustic (the caustic, swept at 64 angles, comes
  * within 4 rho of the centre; the image count differs between the centre and
  * a ring point; min |J| < 0.1 at the centre; or the expansion's error
- * estimate, the gap between its values from the rings (rho/2, rho) and
- * (rho, 2 rho), exceeds 5% of the value) is answered without contour
- * integration when its predicted error is within rel_tol: the expansion's
- * error estimate is below 0.5 rel_tol (mu = A_hex), or the network's
+ * estimate exceeds 5% of the value) is answered without contour integration
+ * when its predicted error is within rel_tol: the expansion's error estimate
+ * (the gap between its values from the rings (rho/2, rho) and (rho, 2 rho),
+ * floored at a twentieth of the finite-source correction |A_hex - A_0|) is
+ * below 0.5 rel_tol (mu = A_hex), or the network's
  * kappa * sigma <= rel_tol (mu = A_hex exp(r)).  All other queries fall back
  * to contour integration (one persistent launch over them, with
  * opts->precision and opts->max_samples).  out[i] receives mu; counts

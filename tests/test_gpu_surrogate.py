@@ -61,11 +61,11 @@ def test_surrogate_with_fallback_matches_oracle(trained):
 
 def test_surrogate_matches_pure_contour_on_sampled_queries(trained):
     path, _ = trained
-    q = P.surrogate_sample(seed=7, n=1 << 16)
+    q = P.surrogate_sample(seed=7, n=1 << 20)
     out, cnt = P.surrogate_mag(path, *q, rel_tol=TOL, details=True)
     ref = P.mag_multi(*q, rel_tol=TOL)  # plain contour integration of every query
     torch.cuda.synchronize()
-    assert cnt["fallback"] + cnt["network"] + cnt["expansion"] == 1 << 16
+    assert cnt["fallback"] + cnt["network"] + cnt["expansion"] == 1 << 20
     r = (out / ref - 1).abs()
     i = int(torch.argmax(torch.nan_to_num(r, nan=1e30)).item())
     worst = [float(t[i]) for t in q] + [float(out[i]), float(ref[i])]
