@@ -43,21 +43,23 @@ sys.path.insert(0, ROOT)
 # (tw_last_launch_work), split by the precision each part runs in.  Counting
 # rules: real add/mul 1, complex add 2, complex mul 6, complex multiply-add 8,
 # reciprocal/division/square root 1.
-#   one Aberth sweep (five roots), FP64 mode: Horner p and p' (5 x 80), the
-#     denominator p' - p S (5 x 8), the division (5 x 12) and the update
-#     (5 x 2) in FP64: 510; the ten pair reciprocals 1/(z_i - z_j), their sums
-#     and the convergence magnitudes in FP32: 225
-#   one Aberth sweep in FP32 (mixed mode): all of it, 760
+#   one Aberth sweep (five roots), FP64 mode: Horner p (5 multiply-adds) and
+#     p' (4) per root (5 x 72), the denominator p' - p S (5 x 8), the
+#     division (5 x 12) and the update (5 x 2) in FP64: 470; the ten pair
+#     reciprocals 1/(z_i - z_j) with their sums (10 x 17) and the convergence
+#     magnitudes (5 x 10) in FP32: 220
+#   one Aberth sweep in FP32 (mixed mode): all of it, 690
 #   one limb sample outside the sweeps: limb point (8), Eq. 6 coefficients
 #     (~100) and per root the two lens reciprocals, f(z) and the residual R
 #     (5 x 23) in FP64: ~225; f', J, dz/dtheta, f'' and z' ^ z'' in FP32
 #     (5 x 45): 225
-#   one FP64 Newton pass over the five roots (mixed mode): 5 x 94 = 470
+#   one FP64 Newton pass over the five roots (kept for the work counter,
+#     which stays zero): 5 x 94 = 470
 #   one edge: image linking distances and 3-5 links of trapezium + parabolic
 #     correction + four error terms: ~145 (FP64), ~20 (FP32)
-F_SWEEP64 = 510.0
-F_SWEEP64_FP32 = 225.0
-F_SWEEP32 = 760.0
+F_SWEEP64 = 470.0
+F_SWEEP64_FP32 = 220.0
+F_SWEEP32 = 690.0
 F_SAMPLE64 = 225.0
 F_SAMPLE32 = 225.0
 F_NEWTON64 = 470.0
