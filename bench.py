@@ -241,19 +241,24 @@ def cpu_oracle_sample(wl, k, seed=777):
 def launched_contour(wl):
     """Whether the last step launched the contour kernel (a surrogate step whose
     queries were all answered without contour integration launches none)."""
+    if wl.get("gate"):
+        return bool(wl["ncontour"]) and wl["ncontour"][-1] > 0
     return wl["kind"] != "surrogate" or (wl["nfb"] and wl["nfb"][-1]["fallback"] > 0)
 
 
 def gpu_launches(wl, steps):
     """Kernels of this library launched in the timed steps: a contour
     integration is two launches (the main pass and the slope-repair pass over
-    the positions it queued, usually none); a surrogate step launches, per
+    the positions it queued, usually none); a gated step launches the feature
+    and gate kernels per chunk of 2^20 positions; a surrogate step launches, per
     chunk of 2^20 queries, the feature, input-layer, three tensor-core GEMM and
     head kernels, then contour integration of its fallbacks (when there are
     any)."""
+    chunks = (wl["n"] + (1 << 20) - 1) >> 20
+    if wl.get("gate"):  # feature and gate kernels per chunk, then the contour pair
+        return sum(2 * chunks + (2 if nc > 0 else 0) for nc in wl["ncontour"][-steps:])
     if wl["kind"] != "surrogate":
         return 2 * steps
-    chunks = (wl["n"] + (1 << 20) - 1) >> 20
     return sum(6 * chunks + (2 if c["fallback"] > 0 else 0) for c in wl["nfb"][-steps:])
 
 
@@ -312,6 +317,8 @@ def main():
     ap.add_argument("--queries", type=int, default=0, help="surrogate workload: query positions")
     ap.add_argument("--autotune", action="store_true", help="let the library choose the launch shape")
     ap.add_argument("--graph", action="store_true", help="replay each launch from a CUDA graph")
+    ap.add_argument("--gate", action="store_true",
+                    help="single-lens workloads: point-source adequacy gate (tw_mag_gated) before contour integration")
     ap.add_argument("--limit", type=int, default=0,
                     help="use a seeded sub-sample of this many positions (small profiling captures)")
     args = ap.parse_args()
@@ -332,6 +339,11 @@ def main():
     cfg = config_of(wl, args.mode, args.gpus)
     cfg["autotune"] = bool(args.autotune)
     cfg["graph"] = bool(args.graph)
+    if args.gate:
+        if wl["kind"] != "mag":
+            raise SystemExit("--gate applies to the single-lens position workloads")
+        cfg["gate"] = True
+        wl["gate"] = True
     if args.impl == "reference":
         run_reference(args, wl, cfg, metric, unit)
         return
@@ -360,7 +372,16 @@ def main():
     def D(a, dt=torch.float64):
         return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
 
-    if wl["kind"] == "mag":
+    if wl["kind"] == "mag" and wl.get("gate"):
+        y1d, y2d = D(wl["y1"]), D(wl["y2"])
+        sd, qd_, rd = (torch.full_like(y1d, wl[k]) for k in ("s", "q", "rho"))
+        outd = torch.empty_like(y1d)
+        wl["ncontour"] = []
+
+        def step():
+            _, nc = P.mag_gated(sd, qd_, rd, y1d, y2d, rel_tol=wl["rel_tol"], precision=prec, out=outd)
+            wl["ncontour"].append(nc)
+    elif wl["kind"] == "mag":
         y1d, y2d = D(wl["y1"]), D(wl["y2"])
         outd = torch.empty_like(y1d)
 
@@ -435,6 +456,8 @@ def main():
         dist.barrier()
     value = world * wl["n"] / t_step
     extra = {}
+    if wl.get("gate"):
+        extra = {"gate": {"contour_fraction": sum(wl["ncontour"][-args.steps:]) / (args.steps * wl["n"])}}
     if wl["kind"] == "surrogate":
         # plain contour integration of the same queries (tw_mag_multi)
         nfb = list(wl["nfb"][-args.steps:])
@@ -454,7 +477,16 @@ def main():
                                "kappa": wl["kappa"]}}
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    if wl["kind"] == "mag":
+    if wl["kind"] == "mag" and wl.get("gate"):
+        hin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+               for a in (np.full(wl["n"], wl["s"]), np.full(wl["n"], wl["q"]), np.full(wl["n"], wl["rho"]),
+                         wl["y1"], wl["y2"])]
+        hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()
+        h2d, d2h = 40 * wl["n"], 8 * wl["n"]
+
+        def e2e_step():
+            P.mag_gated(*[t.numpy() for t in hin], rel_tol=wl["rel_tol"], precision=prec, out=hout.numpy())
+    elif wl["kind"] == "mag":
         hy1 = torch.from_numpy(np.ascontiguousarray(wl["y1"])).pin_memory()
         hy2 = torch.from_numpy(np.ascontiguousarray(wl["y2"])).pin_memory()
         hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()

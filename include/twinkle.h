@@ -205,6 +205,21 @@ int tw_surrogate_mag(const char *weights_path, const double *s, const double *q,
 int tw_surrogate_sample(uint64_t seed, int64_t n, double *s, double *q, double *rho, double *y1, double *y2,
                         void *stream);
 
+/* Magnification with a point-source adequacy gate (not in the paper, which
+ * leaves such tests to other codes, Sec. 2.3; the expansion is the
+ * hexadecapole approximation of Gould 2008 with the error estimate and
+ * near-caustic flag of tw_surrogate_mag, without the network).  For each
+ * position (per-position lens and radius, as tw_mag_multi) the point-source
+ * images at the centre and on three rings give the finite-source expansion
+ * and its error estimate; a position not flagged as near a caustic whose
+ * estimate is within rel_tol / 2 takes the expansion's value, every other
+ * position is integrated by contour (one persistent launch, opts->precision
+ * and opts->max_samples).  *n_contour (optional) receives the number of
+ * contour-integrated positions.  Host or device arrays (all of one kind);
+ * synchronous.  n < 2^31. */
+int tw_mag_gated(const double *s, const double *q, const double *rho, const double *y1, const double *y2, int64_t n,
+                 double rel_tol, double *out, int64_t *n_contour, const tw_opts *opts);
+
 /* C[M][N] = A[M][K] . B[N][K]^T on the tensor cores (tcgen05.mma, BF16
  * inputs, FP32 accumulation and output), the GEMM of the MLP surrogate; the
  * paper has no counterpart.  A, B (bf16, row-major, K contiguous) and C

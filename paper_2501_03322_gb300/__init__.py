@@ -78,6 +78,8 @@ def lib():
             L.tw_lightcurve_ex.argtypes = [d, d, d, d, d, d, d, P, i64, d, P, P]
             L.tw_lightcurve_ex.restype = I
             L.tw_mag_multi.argtypes = [P, P, P, P, P, i64, d, P, P]
+            L.tw_mag_gated.argtypes = [P, P, P, P, P, i64, d, P, P, P]
+            L.tw_mag_gated.restype = I
             L.tw_mag_multi.restype = I
             L.tw_lightcurve_batch.argtypes = [P, P, P, i64, d, P, P]
             L.tw_lightcurve_batch.restype = I
@@ -308,6 +310,21 @@ def mag_multi(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_
                   autotune, use_graph)
     _check(lib().tw_mag_multi(*[_ptr(a) for a in arrs], n, rel_tol, _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
+
+
+def mag_gated(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, max_samples=4096, out=None, stream=None):
+    """Magnification with the point-source adequacy gate (tw_mag_gated): positions
+    whose expansion is certified take its value, the rest are contour-integrated.
+    Returns (out, number of contour-integrated positions)."""
+    arrs = [_prep(a) for a in (s, q, rho, y1, y2)]
+    n = int(arrs[0].shape[0])
+    if out is None:
+        out = _alloc_like(arrs[0], n, np.float64, "float64")
+    o = make_opts(precision, 64, max_samples, _stream_of(arrs[0], stream), None, None, None, False, False)
+    nc = np.zeros(1, np.int64)
+    _check(lib().tw_mag_gated(*[_ptr(a) for a in arrs], n, rel_tol, _ptr(out), nc.ctypes.data_as(ctypes.c_void_p),
+                              ctypes.byref(o)))
+    return out, int(nc[0])
 
 
 def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,

@@ -1093,3 +1093,87 @@ extern "C" int tw_surrogate_sample(uint64_t seed, int64_t n, double *s, double *
     sur_sample_kernel<<<nblk(n, 128), 128, 0, st>>>(seed, n, s, q, rho, y1, y2);
     return cerr(cudaGetLastError());
 }
+
+namespace tw {
+
+// Point-source adequacy gate: a position whose expansion is certified (not
+// flagged as near a caustic, error estimate within rel_tol / 2) takes the
+// expansion's value; every other position is listed for contour integration.
+__global__ void gate_kernel(int64_t n, int64_t row0, const double *MUPS, const uint8_t *FLAG, const float *HEXE,
+                            double tol, double *OUT, int32_t *LIST, unsigned long long *NLIST) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = row0 + i;
+    const double mu = MUPS[g];
+    if (!FLAG[g] && HEXE[g] <= 0.5f * (float)tol && isfinite(mu)) {
+        OUT[g] = mu;
+        atomicAdd(NLIST + 1, 1ull);
+    } else {
+        const unsigned long long slot = atomicAdd(NLIST, 1ull);
+        LIST[slot] = (int32_t)g;
+    }
+}
+
+}  // namespace tw
+
+extern "C" int tw_mag_gated(const double *s, const double *q, const double *rho, const double *y1, const double *y2,
+                            int64_t n, double rel_tol, double *out, int64_t *n_contour, const tw_opts *opts) {
+    if (n < 0 || !(rel_tol > 0) || !isfinite(rel_tol) || n > 0x7fffffffll) return TW_EINVAL;
+    if (n == 0) { if (n_contour) *n_contour = 0; return TW_OK; }
+    if (!s || !q || !rho || !y1 || !y2 || !out) return TW_EINVAL;
+    tw_opts o;
+    tw_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != TW_PREC_FP64 && o.precision != TW_PREC_MIXED) return TW_EINVAL;
+    std::lock_guard<std::mutex> lk(g_sm);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    const bool dev = dev_ptr(out);
+    const double *in[5] = {s, q, rho, y1, y2};
+    for (int k = 0; k < 5; k++)
+        if (dev_ptr(in[k]) != dev) return TW_EINVAL;
+    DevBufs B;
+    const double *din[5];
+    double *dout = out;
+    cudaError_t e;
+    int rc;
+    if (!dev) {  // host arrays: stage through device memory
+        for (int k = 0; k < 5; k++) {
+            double *d;
+            if ((rc = B.get(&d, n))) return rc;
+            if ((e = cudaMemcpyAsync(d, in[k], n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cerr(e);
+            din[k] = d;
+        }
+        if ((rc = B.get(&dout, n))) return rc;
+    } else {
+        for (int k = 0; k < 5; k++) din[k] = in[k];
+    }
+    const int64_t CH = 1 << 20;
+    const int64_t chunk = n < CH ? n : CH;
+    float *X, *HEXE;
+    double *MUPS;
+    uint8_t *FLAG;
+    int32_t *LIST;
+    unsigned long long *NL;
+    if ((rc = B.get(&X, chunk * SXP)) || (rc = B.get(&MUPS, n)) || (rc = B.get(&FLAG, n)) || (rc = B.get(&LIST, n)) ||
+        (rc = B.get(&NL, 2)) || (rc = B.get(&HEXE, n)))
+        return rc;
+    if ((e = cudaMemsetAsync(NL, 0, 16, st)) != cudaSuccess) return cerr(e);
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
+        sur_features_kernel<<<nblk(cn, 128), 128, 0, st>>>(cn, din[0] + c0, din[1] + c0, din[2] + c0, din[3] + c0,
+                                                           din[4] + c0, X, MUPS + c0, FLAG + c0, HEXE + c0);
+        gate_kernel<<<nblk(cn, 256), 256, 0, st>>>(cn, c0, MUPS, FLAG, HEXE, rel_tol, dout, LIST, NL);
+    }
+    unsigned long long cnt[2] = {0, 0};
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, NL, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cerr(e);
+    rc = contour_positions(din[0], din[1], din[2], din[3], din[4], LIST, (int64_t)cnt[0], rel_tol, o.precision,
+                           o.max_samples, dout, nullptr, st);
+    if (rc) return rc;
+    if (!dev && (e = cudaMemcpyAsync(out, dout, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cerr(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cerr(e);
+    if (n_contour) *n_contour = (int64_t)cnt[0];
+    return TW_OK;
+}

@@ -71,6 +71,8 @@ def test_null_pointers_and_empty_calls():
     assert lib.tw_lightcurve(1.0, 1e-3, 1e-3, 0.1, 1.0, 0.0, 20.0, None, 0, 1e-4, None) == P.TW_OK
     assert lib.tw_last_launch_work(None) == P.TW_EINVAL
     assert lib.tw_last_launch_ms(None) == P.TW_EINVAL
+    assert lib.tw_mag_gated(None, None, None, None, None, 3, 1e-4, None, None, None) == P.TW_EINVAL
+    assert lib.tw_mag_gated(None, None, None, None, None, 0, 1e-4, None, None, None) == P.TW_OK
 
 
 def test_batch_offsets_validated_on_host():

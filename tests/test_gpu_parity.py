@@ -262,3 +262,28 @@ def test_central_caustic_set_with_slope_repairs(prec):
     slope = (st & P.POS_SLOPE) != 0
     assert slope.sum() >= 1  # the repair pass is exercised on this set
     assert rel_err(mu[clean & slope], ref[clean & slope]).max() <= TOL
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_point_source_gate(prec):
+    """tw_mag_gated: positions whose expansion is certified take its value, the
+    rest are contour-integrated; every result within the tolerance of the
+    oracle, on the sampled map cells (one lens) and on the oracle-placed
+    queries near the caustics of 8 lenses."""
+    c = W.MAP_PLANETARY
+    rows = load("map_planetary.txt")
+    y1, y2 = W.map_grid()
+    idx = np.array([int(r[0]) for r in rows])
+    ref = np.array([float(r[3]) for r in rows])
+    ok = np.array([int(r[4]) == 0 for r in rows])
+    n = idx.size
+    mu, nc = P.mag_gated(np.full(n, c["s"]), np.full(n, c["q"]), np.full(n, c["rho"]), y1[idx], y2[idx],
+                         rel_tol=c["rel_tol"], precision=prec)
+    assert rel_err(mu[ok], ref[ok]).max() <= TOL
+    assert 0 < nc < n  # both paths are taken
+    rows = load("surrogate_queries.txt")
+    a = np.array([[float(v) for v in r[:6]] for r in rows])
+    ok = np.array([int(r[6]) == 0 for r in rows])
+    mu, nc = P.mag_gated(a[:, 0], a[:, 1], a[:, 2], a[:, 3], a[:, 4], rel_tol=TOL, precision=prec)
+    assert rel_err(mu[ok], a[ok, 5]).max() <= TOL
+    assert 0 <= nc <= len(rows)
