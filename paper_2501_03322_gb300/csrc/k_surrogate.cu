@@ -1114,6 +1114,28 @@ __global__ void gate_kernel(int64_t n, int64_t row0, const double *MUPS, const u
     }
 }
 
+// Grow-only device buffers of tw_mag_gated, one set per device: its calls
+// are serialised (g_sm) and synchronous, so a set is reused call after call
+// instead of being allocated and freed (cudaFree synchronises the device).
+struct GatePool {
+    void *p[12] = {nullptr};
+    size_t sz[12] = {0};
+    template <typename T>
+    int get(int slot, T **out, size_t count) {
+        const size_t need = count * sizeof(T) + 256;
+        if (sz[slot] < need) {
+            if (p[slot]) cudaFree(p[slot]);
+            p[slot] = nullptr;
+            sz[slot] = 0;
+            if (cudaMalloc(&p[slot], need) != cudaSuccess) { (void)cudaGetLastError(); p[slot] = nullptr; return TW_ENOMEM; }
+            sz[slot] = need;
+        }
+        *out = (T *)p[slot];
+        return TW_OK;
+    }
+};
+static GatePool g_gate_pool[64];
+
 }  // namespace tw
 
 extern "C" int tw_mag_gated(const double *s, const double *q, const double *rho, const double *y1, const double *y2,
@@ -1131,7 +1153,9 @@ extern "C" int tw_mag_gated(const double *s, const double *q, const double *rho,
     const double *in[5] = {s, q, rho, y1, y2};
     for (int k = 0; k < 5; k++)
         if (dev_ptr(in[k]) != dev) return TW_EINVAL;
-    DevBufs B;
+    int devno = 0;
+    if (cudaGetDevice(&devno) != cudaSuccess || devno < 0 || devno >= 64) { (void)cudaGetLastError(); return TW_ECUDA; }
+    GatePool &B = g_gate_pool[devno];
     const double *din[5];
     double *dout = out;
     cudaError_t e;
@@ -1139,11 +1163,11 @@ extern "C" int tw_mag_gated(const double *s, const double *q, const double *rho,
     if (!dev) {  // host arrays: stage through device memory
         for (int k = 0; k < 5; k++) {
             double *d;
-            if ((rc = B.get(&d, n))) return rc;
+            if ((rc = B.get(6 + k, &d, n))) return rc;
             if ((e = cudaMemcpyAsync(d, in[k], n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cerr(e);
             din[k] = d;
         }
-        if ((rc = B.get(&dout, n))) return rc;
+        if ((rc = B.get(11, &dout, n))) return rc;
     } else {
         for (int k = 0; k < 5; k++) din[k] = in[k];
     }
@@ -1154,8 +1178,8 @@ extern "C" int tw_mag_gated(const double *s, const double *q, const double *rho,
     uint8_t *FLAG;
     int32_t *LIST;
     unsigned long long *NL;
-    if ((rc = B.get(&X, chunk * SXP)) || (rc = B.get(&MUPS, n)) || (rc = B.get(&FLAG, n)) || (rc = B.get(&LIST, n)) ||
-        (rc = B.get(&NL, 2)) || (rc = B.get(&HEXE, n)))
+    if ((rc = B.get(0, &X, chunk * SXP)) || (rc = B.get(1, &MUPS, n)) || (rc = B.get(2, &FLAG, n)) ||
+        (rc = B.get(3, &LIST, n)) || (rc = B.get(4, &NL, 2)) || (rc = B.get(5, &HEXE, n)))
         return rc;
     if ((e = cudaMemsetAsync(NL, 0, 16, st)) != cudaSuccess) return cerr(e);
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
