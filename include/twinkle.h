@@ -216,7 +216,9 @@ int tw_surrogate_sample(uint64_t seed, int64_t n, double *s, double *q, double *
  * position is integrated by contour (one persistent launch, opts->precision
  * and opts->max_samples).  *n_contour (optional) receives the number of
  * contour-integrated positions.  Host or device arrays (all of one kind);
- * synchronous.  n < 2^31. */
+ * synchronous.  n < 2^31.  The library keeps the call's device buffers
+ * (about 60 B per position, plus 48 B per position for host arrays) for the
+ * next call on the same device. */
 int tw_mag_gated(const double *s, const double *q, const double *rho, const double *y1, const double *y2, int64_t n,
                  double rel_tol, double *out, int64_t *n_contour, const tw_opts *opts);
 
