@@ -14,6 +14,7 @@ source; in short:
 * ``mag``          -- magnification = image area / source area (Sec. 1), image
                       area by a linking-free contour integral (Eq. 8)
 * ``crossings``    -- limb/caustic crossing angles, by the caustic or an image-count scan
+* ``close_approaches`` -- limb angles where the caustic nearly touches the limb
 * ``caustic``      -- critical curve J = 0 and its caustic image
 * ``trajectory``   -- straight-line source trajectory of a light curve
 * ``rayshoot``     -- brute-force inverse ray shooting (Sec. 1), for pinning ``mag``
@@ -73,6 +74,8 @@ def _load():
         lib.orc_caustic.restype = ctypes.c_int
         lib.orc_crossings.argtypes = [d, d, d, d, d, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
         lib.orc_crossings.restype = ctypes.c_int
+        lib.orc_close_approaches.argtypes = [d, d, d, d, d, P, ctypes.c_int]
+        lib.orc_close_approaches.restype = ctypes.c_int
         lib.orc_mag.argtypes = [d, d, d, P, P, i64, ctypes.c_int, ctypes.c_int, P, P, P]
         lib.orc_mag.restype = ctypes.c_int
         lib.orc_trajectory.argtypes = [d, d, d, d, P, i64, P, P]
@@ -141,6 +144,16 @@ def crossings(s: float, q: float, rho: float, y1: float, y2: float, method: str 
     return np.sort(out[: min(n, 64)])
 
 
+def close_approaches(s: float, q: float, rho: float, y1: float, y2: float) -> np.ndarray:
+    """Limb angles where the caustic comes within 5% of rho of the limb without
+    crossing it (the extra split points of the quadrature in ``mag``)."""
+    out = np.zeros(64)
+    n = _load().orc_close_approaches(s, q, rho, y1, y2, _ptr(out), 64)
+    if n < 0:
+        raise RuntimeError("oracle caustic failed")
+    return np.sort(out[: min(n, 64)])
+
+
 def mag(s: float, q: float, rho: float, y1, y2, scan_K: int = 256, nthreads: int = 0):
     """Finite-source magnifications of positions (y1[i], y2[i]).
 
@@ -157,6 +170,28 @@ def mag(s: float, q: float, rho: float, y1, y2, scan_K: int = 256, nthreads: int
     if rc:
         raise ValueError("oracle: invalid lens or source parameters")
     return out, st, nx
+
+
+def sample_near_caustic(n: int, seed: int):
+    """n positions of the surrogate workload's distribution, drawn on the CPU:
+    a lens with log10 s ~ U[-0.5, 0.5], log10 q ~ U[-5, -1], log10 rho ~
+    U[-4, -2] per position, a random point of a random branch of its caustic
+    (this oracle's, 256 angles), displaced uniformly within a disc of three
+    times that branch's bounding-box size.  Returns (s, q, rho, y1, y2)."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((5, n))
+    for i in range(n):
+        s = 10 ** rng.uniform(-0.5, 0.5)
+        q = 10 ** rng.uniform(-5, -1)
+        rho = 10 ** rng.uniform(-4, -2)
+        _, cc = caustic(s, q, 256)
+        b = rng.integers(4)
+        c = cc[rng.integers(256), b]
+        w = max(np.ptp(cc[:, b].real), np.ptp(cc[:, b].imag))
+        r = 3 * w * np.sqrt(rng.uniform())
+        a = rng.uniform(0, 2 * np.pi)
+        out[:, i] = (s, q, rho, c.real + r * np.cos(a), c.imag + r * np.sin(a))
+    return tuple(out)
 
 
 def trajectory(u0: float, alpha: float, t0: float, tE: float, times):

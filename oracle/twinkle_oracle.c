@@ -46,9 +46,17 @@
  *     residuals (Sec. 2.4.1, consequence of Eq. 13-15);
  *   - parity and image derivative: Eq. 7 and dz/dtheta from differentiating
  *     Eq. 1 (Eq. 10 prints f' where its complex conjugate is meant);
+ *   - real images refined by Newton's method on the lens equation itself
+ *     (Eq. 1; conditioning 1/|J|) after classification: a root of the
+ *     generically expanded quintic inside a cluster of roots next to a cusp
+ *     is only good to eps B/|p'|, and that noise, amplified by 1/|J|, kept
+ *     the quadrature from converging there;
  *   - caustic crossings: intersections of the limb with the caustic, the image
  *     of the critical curve J = 0 (Eq. 7), cross-checked by scanning the image
- *     count along the limb.
+ *     count along the limb;
+ *   - close approaches of the caustic to the limb that do not cross it (a
+ *     limb grazing a cusp) split the quadrature as well: the point-source
+ *     magnification peaks there with a width of about distance/rho.
  *
  * Arithmetic is long double throughout (x87 80-bit on x86-64, IEEE binary128
  * on AArch64).  The generic expansion is exposed to the catastrophic
@@ -362,8 +370,36 @@ typedef struct {
     long budget; /* integrand evaluations allowed before giving up refinement */
 } ctx_t;
 
+/* Newton refinement of a real image z of the source point zeta on the lens
+ * equation itself (Eq. 1), after classification.  A root of the generically
+ * expanded quintic inside a cluster of roots (several images and ghosts
+ * within a small distance, next to a cusp) is only accurate to about
+ * eps B/|p'(z)|, far above the round-off of Eq. 1, whose conditioning at an
+ * image is 1/|J| (Eq. 7).  With R = zeta - z - conj(f(z)) (Eq. 12) the
+ * linearised equation dz + conj(f') conj(dz) = R gives
+ *     dz = (R - conj(f') conj(R)) / J.
+ * A step is kept only while it lowers |R| and stays well inside the distance
+ * `sep` to the nearest other root, so that no image is moved onto another. */
+static cplx polish_image(const lens_t *L, cplx zeta, cplx z, real sep) {
+    for (int it = 0; it < 4; it++) {
+        cplx f, f1;
+        lens_f(L, z, &f, &f1, NULL);
+        cplx R = zeta - z - c_conj(f);
+        real J = 1.0 - c_re(f1) * c_re(f1) - c_im(f1) * c_im(f1);
+        if (J == 0 || c_abs(R) == 0) break;
+        cplx dz = (R - c_conj(f1) * c_conj(R)) / J;
+        if (!(c_abs(dz) < 0.1 * sep)) break;
+        cplx zn = z + dz, fn;
+        lens_f(L, zn, &fn, NULL, NULL);
+        if (!(c_abs(zeta - zn - c_conj(fn)) < c_abs(R))) break;
+        z = zn;
+    }
+    return z;
+}
+
 /* 1/2 sum_{real j} p_j (z_j - w) ^ dz_j/dtheta at limb angle theta, the real
- * images being the `count` roots of smallest residual.  With
+ * images being the `count` roots of smallest residual, each refined on the
+ * lens equation (polish_image).  With
  * dz/dtheta = (zeta' - conj(f') conj(zeta'))/J and p = sign J,
  * p (z - w) ^ z' = Im(conj(z - w) (zeta' - conj(f') conj(zeta'))) / |J|.
  * Optionally returns S = sum_j p_j z_j. */
@@ -380,7 +416,11 @@ static real integrand(ctx_t *X, real theta, int count, cplx w, cplx *S_out) {
     real g = 0;
     cplx S = 0;
     for (int k = 0; k < count; k++) {
-        cplx z = P.r[P.order[k]];
+        const int i = P.order[k];
+        real sep = INFINITY;
+        for (int j = 0; j < 5; j++)
+            if (j != i && c_abs(P.r[j] - P.r[i]) < sep) sep = c_abs(P.r[j] - P.r[i]);
+        cplx z = polish_image(&X->L, zeta, P.r[i], sep);
         cplx f1;
         lens_f(&X->L, z, NULL, &f1, NULL);
         real J = 1.0 - c_re(f1) * c_re(f1) - c_im(f1) * c_im(f1);
@@ -571,12 +611,32 @@ static cplx bisect_branch(const lens_t *L, cplx zeta0, real rho, real pa, cplx z
     return 0.5 * (za + zb);
 }
 
+/* Limb angle of the point nearest to zc (the direction of zc from the source
+ * centre). */
+static real limb_angle(cplx zeta0, cplx zc) {
+    cplx d = zc - zeta0;
+    real th = r_atan2(c_im(d), c_re(d));
+    return th < 0 ? th + TWO_PI_L : th;
+}
+
+/* A close approach of the caustic to the limb, closer than NEAR_FRAC * rho,
+ * makes the point-source magnification along the limb peak sharply (width
+ * about distance/rho in angle) where no image count changes; its angle is
+ * recorded as a split point of the quadrature (tanh-sinh resolves features at
+ * the end of an interval, not inside it). */
+#define NEAR_FRAC 0.05
+#define MAX_SPLIT 64
+
 /* Method (ii): limb/caustic intersections.  Sign changes of the limb distance
  * along each tracked branch are bisected; local minima of |distance| that do
  * not change sign between grid points are searched (golden section) for a
- * pair of crossings hidden inside one grid cell. */
-static int crossings_caustic(const lens_t *L, const crit_t *C, cplx zeta0, real rho, xing_t *xs) {
+ * pair of crossings hidden inside one grid cell.  Minima that stay on one side
+ * but come within NEAR_FRAC * rho of the limb are returned in splits[] (limb
+ * angles, *nsplit of them) when splits is not NULL. */
+static int crossings_caustic(const lens_t *L, const crit_t *C, cplx zeta0, real rho, xing_t *xs, real *splits,
+                             int *nsplit) {
     int nx = 0, M = C->M;
+    if (nsplit) *nsplit = 0;
     real *d = (real *)malloc(sizeof(real) * 4 * M);
     if (!d) return -1;
     for (int i = 0; i < 4 * M; i++) d[i] = c_abs(C->cc[i] - zeta0) - rho;
@@ -599,10 +659,11 @@ static int crossings_caustic(const lens_t *L, const crit_t *C, cplx zeta0, real 
             }
             real dp = d[4 * kp + bp];
             if (!((dp < 0) == (da < 0) && r_abs(da) <= r_abs(dp) && r_abs(da) <= r_abs(db))) continue;
+            const int near = splits && r_abs(da) < 4.0 * NEAR_FRAC * rho;
             /* skip minima whose parabola through the three grid values stays
-             * well away from zero */
+             * well away from zero (unless the approach is close) */
             real curv = dp - 2.0 * da + db;
-            if (curv != 0) {
+            if (curv != 0 && !near) {
                 real vmin = da - (db - dp) * (db - dp) / (8.0 * curv);
                 if (r_abs(vmin) > 0.5 * r_abs(da) && (vmin < 0) == (da < 0)) continue;
             }
@@ -631,6 +692,11 @@ static int crossings_caustic(const lens_t *L, const crit_t *C, cplx zeta0, real 
                 real plo = TWO_PI_L * (k - 1) / M, phi_hi = TWO_PI_L * (k + 1) / M;
                 add_xing(xs, &nx, L, zeta0, bisect_branch(L, zeta0, rho, plo, zlo, pmin, zmin));
                 add_xing(xs, &nx, L, zeta0, bisect_branch(L, zeta0, rho, pmin, zmin, phi_hi, zhi));
+            } else if (near) {
+                /* no crossing: the closest approach is a split point */
+                real fm = f1 < f2 ? f1 : f2;
+                cplx zm = f1 < f2 ? g1 : g2;
+                if (fm < NEAR_FRAC * rho && *nsplit < MAX_SPLIT) splits[(*nsplit)++] = limb_angle(zeta0, lens_map(L, zm));
             }
         }
     }
@@ -659,7 +725,11 @@ static int count_at(ctx_t *X, real theta) {
 }
 
 /* Method (i): changes of the image count on a uniform grid of K limb angles,
- * each bisected to full precision.  Returns the number found. */
+ * each bisected to full precision.  A change is kept only if the count
+ * differs between the two sides at 1e-10 and 1e-8 rad from it: where many
+ * images sit next to a critical curve, the residual test can misjudge an
+ * isolated angle, and bisection can settle on such a point instead of the
+ * crossing.  Returns the number found. */
 static int crossings_scan(ctx_t *X, int K, real *out, int maxout) {
     int n = 0;
     int c0 = count_at(X, 0), cprev = c0;
@@ -673,8 +743,14 @@ static int crossings_scan(ctx_t *X, int K, real *out, int maxout) {
                 if (m == a || m == b) break;
                 if (count_at(X, m) == cprev) a = m; else b = m;
             }
-            if (n < maxout) out[n] = 0.5 * (a + b);
-            n++;
+            real x = 0.5 * (a + b);
+            int real_change = 1;
+            for (real dd = 1e-10; dd < 2e-8; dd *= 100)
+                if (count_at(X, x - dd) == count_at(X, x + dd)) real_change = 0;
+            if (real_change) {
+                if (n < maxout) out[n] = x;
+                n++;
+            }
         }
         cprev = c;
     }
@@ -688,6 +764,31 @@ typedef struct {
     long nevals;
 } mag_info_t;
 
+/* Integral over one piece [a, b] of the limb (b > a) with `count` images,
+ * whose ends are crossings with critical points wa (at a) and wb (at b).
+ * Interior split angles sp[0..ns-1] (ascending, inside (a, b)) cut it into
+ * sub-arcs: the first is integrated about wa, the last about wb, the others
+ * about the origin; with none, the piece is cut at its midpoint.  For a
+ * sub-arc [u, v] integrated about w,
+ *   Int 1/2 sum p z ^ dz = Int 1/2 sum p (z - w) ^ dz + 1/2 w ^ [S(v) - S(u)],
+ * and the terms at the crossings cancel against the neighbouring pieces (S is
+ * continuous there and both sides use the same w), so what is added here is
+ * 1/2 wa ^ S(first cut) - 1/2 wb ^ S(last cut). */
+static real piece_integral(ctx_t *X, real a, real b, int count, cplx wa, cplx wb, const real *sp, int ns, real tol) {
+    real mid = 0.5 * (a + b);
+    real c0 = ns ? sp[0] : mid, c1 = ns ? sp[ns - 1] : mid;
+    real tsub = tol / (ns + 2);
+    real A = ts_rule(X, a, c0, count, wa, tsub, 40);
+    for (int k = 0; k + 1 < ns; k++) A += ts_rule(X, sp[k], sp[k + 1], count, 0, tsub, 40);
+    A += ts_rule(X, c1, b, count, wb, tsub, 40);
+    cplx S0, S1;
+    (void)integrand(X, c0, count, 0, &S0);
+    (void)integrand(X, c1, count, 0, &S1);
+    A += 0.5 * (c_re(wa) * c_im(S0) - c_im(wa) * c_re(S0));
+    A -= 0.5 * (c_re(wb) * c_im(S1) - c_im(wb) * c_re(S1));
+    return A;
+}
+
 static real mag_one(const lens_t *L, const crit_t *C, real y1, real y2, real rho, int scan_K, mag_info_t *info) {
     ctx_t X;
     X.L = *L;
@@ -695,17 +796,30 @@ static real mag_one(const lens_t *L, const crit_t *C, real y1, real y2, real rho
     X.rho = rho;
     X.status = ORC_OK;
     X.nevals = 0;
-    X.budget = 400000;
+    X.budget = 1000000;
     xing_t xs[MAX_XING];
-    int nx = crossings_caustic(L, C, X.zeta0, rho, xs);
+    real sp[MAX_SPLIT];
+    int nsp = 0;
+    int nx = crossings_caustic(L, C, X.zeta0, rho, xs, sp, &nsp);
     if (nx < 0) nx = 0;
     if (nx % 2) X.status = ORC_XING;
+    for (int i = 1; i < nsp; i++) /* split angles in ascending order */
+        for (int k = i; k > 0 && sp[k] < sp[k - 1]; k--) {
+            real t = sp[k]; sp[k] = sp[k - 1]; sp[k - 1] = t;
+        }
     /* absolute tolerance: 1e-12 of the source area, per piece */
     real tol = 1e-12 * PI_L * rho * rho;
     real A = 0;
-    if (nx < 2) {
+    if (nx < 2 && nsp == 0) {
         int count = count_at(&X, 0);
         A = periodic_rule(&X, count, tol);
+    } else if (nx < 2) {
+        /* no crossing, close approaches: tanh-sinh over the arcs between them */
+        int count = count_at(&X, sp[0]);
+        for (int k = 0; k < nsp; k++) {
+            real a = sp[k], b = (k + 1 < nsp) ? sp[k + 1] : sp[0] + TWO_PI_L;
+            if (b - a > 1e-30) A += ts_rule(&X, a, b, count, 0, tol / nsp, 40);
+        }
     } else {
         int counts[MAX_XING];
         for (int i = 0; i < nx; i++) {
@@ -714,12 +828,18 @@ static real mag_one(const lens_t *L, const crit_t *C, real y1, real y2, real rho
             real mid = 0.5 * (a + b);
             counts[i] = count_at(&X, mid);
             cplx wa = xs[i].zc, wb = xs[(i + 1) % nx].zc;
-            A += ts_rule(&X, a, mid, counts[i], wa, tol, 12);
-            A += ts_rule(&X, mid, b, counts[i], wb, tol, 12);
-            cplx S;
-            (void)integrand(&X, mid, counts[i], 0, &S);
-            cplx dw = wa - wb;
-            A += 0.5 * (c_re(dw) * c_im(S) - c_im(dw) * c_re(S));
+            /* split angles strictly inside the piece */
+            real ins[MAX_SPLIT];
+            int nin = 0;
+            for (int k = 0; k < nsp; k++) {
+                real t = sp[k] < a ? sp[k] + TWO_PI_L : sp[k];
+                if (t > a + 1e-12 * (b - a) && t < b - 1e-12 * (b - a)) ins[nin++] = t;
+            }
+            for (int u = 1; u < nin; u++)
+                for (int k = u; k > 0 && ins[k] < ins[k - 1]; k--) {
+                    real t = ins[k]; ins[k] = ins[k - 1]; ins[k - 1] = t;
+                }
+            A += piece_integral(&X, a, b, counts[i], wa, wb, ins, nin, tol);
         }
         /* consecutive pieces must alternate between 3 and 5 images */
         for (int i = 0; i < nx; i++) {
@@ -809,7 +929,7 @@ int orc_crossings(double s, double q, double rho, double y1, double y2, int meth
         crit_t C;
         if (crit_build(&L, K, &C) != 0) { crit_free(&C); return -1; }
         xing_t xs[MAX_XING];
-        int n = crossings_caustic(&L, &C, cmk(y1, y2), rho, xs);
+        int n = crossings_caustic(&L, &C, cmk(y1, y2), rho, xs, NULL, NULL);
         for (int i = 0; i < n && i < maxout; i++) out[i] = (double)xs[i].theta;
         crit_free(&C);
         return n;
@@ -825,6 +945,22 @@ int orc_crossings(double s, double q, double rho, double y1, double y2, int meth
     int n = crossings_scan(&X, K, tmp, MAX_XING);
     for (int i = 0; i < n && i < maxout && i < MAX_XING; i++) out[i] = (double)tmp[i];
     return n;
+}
+
+/* Close approaches of the caustic to one limb that do not cross it (limb
+ * angles, at most maxout); returns their number.  These are the split points
+ * of the quadrature in mag_one. */
+int orc_close_approaches(double s, double q, double rho, double y1, double y2, double *out, int maxout) {
+    lens_t L = lens_make(s, q);
+    crit_t C;
+    if (crit_build(&L, 4096, &C) != 0) { crit_free(&C); return -1; }
+    xing_t xs[MAX_XING];
+    real sp[MAX_SPLIT];
+    int nsp = 0;
+    (void)crossings_caustic(&L, &C, cmk(y1, y2), rho, xs, sp, &nsp);
+    for (int i = 0; i < nsp && i < maxout; i++) out[i] = (double)sp[i];
+    crit_free(&C);
+    return nsp;
 }
 
 /* Finite-source magnifications of n positions sharing one lens and source

@@ -255,3 +255,71 @@ def test_slope_premise(cfg):
             assert cos < 1e-2 and abs(abs(d5) / abs(d3) - 1) < 1e-2, (th, dth, cos)
             e5, _ = _merging_pairs(s, q, z0, rho, th, 2 * dth)
             assert abs((d5 * np.conj(e5)).real) / (abs(d5) * abs(e5)) > 0.99
+
+
+def _point_mag_sum(s, q, zeta, count):
+    """Point-source magnification sum_j 1/|J_j| (Eq. 7) over the `count`
+    roots of smallest lens-equation residual (Eq. 12) at source point zeta."""
+    im = O.images(s, q, zeta)
+    real = np.argsort(np.abs(im["residuals"]))[:count]
+    return float(np.sum(1.0 / np.abs(im["jac"][real])))
+
+
+def _limb_mean_point_mag(s, q, rho, y1, y2):
+    """(1/2 pi) Int_0^{2 pi} mu_ps(zeta0 + rho e^{i theta}) d theta by adaptive
+    Gauss-Kronrod quadrature (QUADPACK) on each arc between caustic crossings.
+    At a crossing the two merging images have 1/|J| ~ 1/sqrt(theta - a), an
+    end-point singularity the extrapolation of QUADPACK absorbs; where the
+    caustic nearly touches the limb the integrand peaks sharply, so those
+    angles are given as break points."""
+    from scipy.integrate import quad
+
+    z0 = complex(y1, y2)
+    xs = O.crossings(s, q, rho, y1, y2, "caustic", 2048)
+    near = O.close_approaches(s, q, rho, y1, y2)
+    arcs = [(xs[i], xs[i + 1] if i + 1 < len(xs) else xs[0] + 2 * np.pi) for i in range(len(xs))]
+    if not arcs:
+        arcs = [(near[0], near[0] + 2 * np.pi)] if len(near) else [(0.0, 2 * np.pi)]
+    tot = 0.0
+    for a, b in arcs:
+        c = O.images(s, q, z0 + rho * np.exp(1j * 0.5 * (a + b)))["count"]
+        pts = sorted(t + 2 * np.pi * k for t in near for k in (0, 1) if a < t + 2 * np.pi * k < b)
+
+        def f(x):
+            return _point_mag_sum(s, q, z0 + rho * np.exp(1j * x), c)
+
+        val, _ = quad(f, a, b, points=pts or None, epsabs=0.0, epsrel=1e-10, limit=4000)
+        tot += val
+    return tot / (2 * np.pi)
+
+
+@pytest.mark.parametrize(
+    "s,q,rho,y1,y2",
+    [
+        (1.0, 0.1, 0.1, 0.2, 0.2),  # Fig. 2 configuration: two fold crossings
+        (1.0, 0.5, 0.05, 0.09635215498703824, 0.5675190958091779),  # resonant large source, four crossings
+        (3.0, 1e-4, 1.1e-4, -0.00017032196187594936, -5.5429363083667814e-05),  # central caustic next to a cusp, mu ~ 1e4
+        (0.5, 1e-6, 1e-4, -1.49998960, -0.0035),  # Fig. 5 spike position (Sec. 4.2): limb grazing a cusp
+        (0.8, 0.3, 0.02, 0.5, 0.3),  # no crossing
+    ],
+)
+def test_area_derivative_identity(s, q, rho, y1, y2):
+    """pi rho^2 mu(rho) is the integral of the point-source magnification over
+    the disc of radius rho (Sec. 1), so d(rho^2 mu)/d rho = 2 rho <mu_ps>, the
+    mean over the limb circle.  The left side differentiates the oracle's
+    contour integral (its crossing pieces, the integration about critical
+    points and their boundary terms, Eq. 8-11) in rho; the right side sums
+    point-source magnifications 1/|J| directly, with no contour, linking or
+    area formula.  A wrong sign, factor or piece in the assembly changes mu
+    differently at each rho and breaks the equality."""
+    import concurrent.futures as cf
+
+    h = 1e-3
+    radii = rho * np.array([1 - 2 * h, 1 - h, 1 + h, 1 + 2 * h])
+    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+        res = list(ex.map(lambda r: O.mag(s, q, r, [y1], [y2], scan_K=0, nthreads=1), radii))
+    assert all(int(r[1][0]) == 0 for r in res)
+    g = [r * r * m[0][0] for r, m in zip(radii, res)]
+    dg = (-g[3] + 8 * g[2] - 8 * g[1] + g[0]) / (12 * h * rho)
+    mean = _limb_mean_point_mag(s, q, rho, y1, y2)
+    assert abs(dg / (2 * rho * mean) - 1) < 1e-7
