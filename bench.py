@@ -57,6 +57,19 @@ sys.path.insert(0, ROOT)
 #     which stays zero): 5 x 94 = 470
 #   one edge: image linking distances and 3-5 links of trapezium + parabolic
 #     correction + four error terms: ~145 (FP64), ~20 (FP32)
+# Feature kernel of the surrogate (point images at the query centre and at 24
+# ring points, caustic sweep): per point solve outside its sweeps, Eq. 6
+# coefficients (~100), their FP32 scaling (12) and per root the two lens
+# reciprocals, the residual and f', J (5 x 47) in FP64: ~357, and ~30 FP32;
+# per FP32 Aberth sweep 690 (as above); per FP64 Newton root step Horner p and
+# p' (72), the division (12) and the update (2): 86; per Aberth iteration of
+# the caustic quartic in FP32, six pair reciprocals with their sums (6 x 13)
+# and four roots of Horner, division and magnitudes (4 x 85) plus the update:
+# ~430.
+F_FEAT_SOLVE64 = 357.0
+F_FEAT_SOLVE32 = 30.0
+F_FEAT_NEWTON64 = 86.0
+F_CAUSTIC32 = 430.0
 F_SWEEP64 = 470.0
 F_SWEEP64_FP32 = 220.0
 F_SWEEP32 = 690.0
@@ -65,10 +78,15 @@ F_SAMPLE32 = 225.0
 F_NEWTON64 = 470.0
 F_EDGE64 = 145.0
 F_EDGE32 = 20.0
-# Peaks (FLOP/s).  FP64: GB300's nominal FP64 rate (1.25 TFLOP/s); FP32: 152 SMs
-# x 128 FP32 lanes x 2 FLOP/FMA x 2.07 GHz maximum SM clock.
-PEAK_FP64 = 1.25e12
-PEAK_FP32 = 152 * 128 * 2 * 2.07e9
+# Nominal peaks (FLOP/s), context only: FP64 GB300's nominal 1.25 TFLOP/s (152
+# SMs x 2.07 GHz x 2 FP64 FMA per clock per SM x 2 FLOP); FP32 152 SMs x 128
+# lanes x 2 FLOP x 2.07 GHz.  These unit-count peaks are the roofline's
+# denominators; the FMA-chain probe (tw_peak_probe) is reported beside them
+# (all SMs running FP64 FMAs draw enough power to lower the clock, to about
+# 1.06 TFLOP/s).  The tensor-core GEMM uses the bf16 peak of
+# MEASURED_PEAKS.json (sustained: the GEMMs run inside a seconds-long step).
+NOMINAL_FP64 = 1.25e12
+NOMINAL_FP32 = 152 * 128 * 2 * 2.07e9
 
 
 def workload(name):
@@ -198,29 +216,81 @@ def flops_of(work, mode):
     return f64, f32
 
 
-def surrogate_oracle_queries():
-    """Positions near caustics placed by the oracle (tests/golden/surrogate_queries.txt)."""
-    path = os.path.join(ROOT, "tests", "golden", "surrogate_queries.txt")
-    rows = [ln.split() for ln in open(path) if not ln.startswith("#") and ln.strip()]
-    return np.array([[float(v) for v in r[:5]] for r in rows])
+GOLD = os.path.join(ROOT, "tests", "golden")
 
 
-def cpu_oracle_sample(wl, k, seed=777):
-    """Time the CPU oracle on k positions of the workload using every host core."""
+def golden_rows(name):
+    """Rows of a stored oracle file (tests/golden, written by the oracle only)."""
+    return [ln.split() for ln in open(os.path.join(GOLD, name)) if not ln.startswith("#") and ln.strip()]
+
+
+def golden_errors(wl, prec, P, wpath=None):
+    """Relative error of the GPU path against the oracle's stored values on the
+    workload's golden positions, in the benchmark's call path and mode: max,
+    99.9th percentile, the fraction of positions whose error estimate bounds
+    the true error (contour paths), and the number of positions compared."""
+    from paper_2501_03322_gb300 import workloads as W
+
+    err_est = None
+    if wl["kind"] == "surrogate":
+        a = np.array([[float(v) for v in r[:7]] for r in golden_rows("surrogate_queries.txt")])
+        ok = a[:, 6] == 0
+        got, _ = P.surrogate_mag(wpath, *[a[ok, k].copy() for k in range(5)], rel_tol=wl["rel_tol"],
+                                 kappa=wl["kappa"], precision=prec)
+        ref, name = a[ok, 5], "surrogate_queries.txt"
+    elif wl["kind"] == "mag":
+        name = "stress_resonant_1e4.txt" if wl["name"].startswith("stress") else "map_planetary.txt"
+        rows = [r for r in golden_rows(name) if int(r[4]) == 0]
+        y1 = np.array([float(r[1]) for r in rows])
+        y2 = np.array([float(r[2]) for r in rows])
+        ref = np.array([float(r[3]) for r in rows])
+        got, err_est, _, _ = P.mag(wl["s"], wl["q"], wl["rho"], y1, y2, rel_tol=wl["rel_tol"], precision=prec,
+                                   details=True)
+    elif wl["kind"] == "lc":
+        name = "lightcurve_central.txt"
+        rows = [r for r in golden_rows(name) if int(r[2]) == 0]
+        t = np.array([float(r[0]) for r in rows])
+        ref = np.array([float(r[1]) for r in rows])
+        got, err_est, _, _ = P.lightcurve(wl["s"], wl["q"], wl["rho"], wl["u0"], wl["alpha"], wl["t0"], wl["tE"], t,
+                                          rel_tol=wl["rel_tol"], precision=prec, details=True)
+    else:
+        name = "batch_lightcurves.txt"
+        rows = [r for r in golden_rows(name) if int(r[4]) == 0]
+        curves = np.array([int(r[0]) for r in rows])
+        t = np.array([float(r[2]) for r in rows])
+        ref = np.array([float(r[3]) for r in rows])
+        # the golden points as a batch of their own curves, one time each
+        params = wl["params"][curves]
+        offsets = np.arange(len(rows) + 1, dtype=np.int64)
+        got, err_est, _, _ = P.lightcurve_batch(params, offsets, t, rel_tol=wl["rel_tol"], precision=prec,
+                                                details=True)
+    rel = np.abs(np.asarray(got) / ref - 1.0)
+    out = {"golden": name, "positions": int(rel.size), "max_rel_err": float(rel.max()),
+           "p999_rel_err": float(np.quantile(rel, 0.999)), "rel_tol": wl["rel_tol"]}
+    if err_est is not None:
+        out["estimate_bounds_error"] = float(np.mean(np.abs(np.asarray(got) - ref) <= np.asarray(err_est)
+                                                     + 1e-12 * ref))
+    return out
+
+
+def cpu_oracle_sample(wl, k, seed=777, cores=None):
+    """Time the CPU oracle on k positions of the workload on `cores` host
+    threads (all by default).  Surrogate queries are drawn on the CPU from the
+    benchmark's own distribution (oracle.sample_near_caustic); every other
+    workload uses a seeded subset of its own positions."""
     import concurrent.futures as cf
 
     import oracle as O
     from paper_2501_03322_gb300 import workloads as W
 
-    cores = os.cpu_count() or 1
+    cores = cores or os.cpu_count() or 1
     if wl["kind"] == "surrogate":
         # one lens per query: spread the queries over the cores
-        a = surrogate_oracle_queries()
-        idx = W.sample_indices(len(a), k, seed=seed)
+        a = np.array(O.sample_near_caustic(k, seed)).T
         t0 = time.perf_counter()
         with cf.ThreadPoolExecutor(max_workers=cores) as ex:
-            list(ex.map(lambda r: O.mag(r[0], r[1], r[2], [r[3]], [r[4]], nthreads=1), a[idx]))
-        return len(idx), time.perf_counter() - t0, cores
+            list(ex.map(lambda r: O.mag(r[0], r[1], r[2], [r[3]], [r[4]], nthreads=1), a))
+        return len(a), time.perf_counter() - t0, cores
     idx = W.sample_indices(int(wl["n"]), k, seed=seed)
     t0 = time.perf_counter()
     if wl["kind"] == "mag":
@@ -260,6 +330,15 @@ def gpu_launches(wl, steps):
     if wl["kind"] != "surrogate":
         return 2 * steps
     return sum(6 * chunks + (2 if c["fallback"] > 0 else 0) for c in wl["nfb"][-steps:])
+
+
+def load_peaks():
+    """MEASURED_PEAKS.json (driver-written), or {} when absent."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
 
 
 def max_over_ranks(x, dist, device):
@@ -310,7 +389,7 @@ def main():
                     choices=["map_planetary", "lightcurve_central", "stress_resonant", "batch_lightcurves",
                              "surrogate"])
     ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--cpu-sample", type=int, default=128, help="positions in the CPU oracle baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=64, help="positions in the CPU oracle baseline sample")
     ap.add_argument("--ref-sample", type=int, default=24, help="positions per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-samples", type=int, default=0, help="surrogate workload: training positions")
@@ -413,10 +492,13 @@ def main():
         outd = torch.empty(wl["n"], dtype=torch.float64, device=dev)
         wl["nfb"] = []
 
+        wl["sur_stats"] = []
+
         def step():
             _, cnt = P.surrogate_mag(wpath, *qd, rel_tol=wl["rel_tol"], kappa=wl["kappa"], precision=prec, out=outd,
                                      details=True)
             wl["nfb"].append(cnt)
+            wl["sur_stats"].append(P.last_surrogate_stats())
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
@@ -459,20 +541,32 @@ def main():
     if wl.get("gate"):
         extra = {"gate": {"contour_fraction": sum(wl["ncontour"][-args.steps:]) / (args.steps * wl["n"])}}
     if wl["kind"] == "surrogate":
-        # plain contour integration of the same queries (tw_mag_multi)
+        # plain contour integration of the same queries (tw_mag_multi), in the
+        # arm's own mode and in FP64
         nfb = list(wl["nfb"][-args.steps:])
-        pe = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        flush.zero_()
-        pe[0].record(stream)
-        P.mag_multi(*qd, rel_tol=wl["rel_tol"], precision=prec, out=outd)
-        pe[1].record(stream)
-        pe[1].synchronize()
-        t_plain = pe[0].elapsed_time(pe[1]) / 1e3
-        extra = {"surrogate": {"fallback_fraction": sum(c["fallback"] for c in nfb) / (len(nfb) * wl["n"]),
-                               "network_fraction": sum(c["network"] for c in nfb) / (len(nfb) * wl["n"]),
-                               "expansion_fraction": sum(c["expansion"] for c in nfb) / (len(nfb) * wl["n"]),
+        sst = list(wl["sur_stats"][-args.steps:])
+
+        def plain(pr):
+            pe = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            flush.zero_()
+            pe[0].record(stream)
+            P.mag_multi(*qd, rel_tol=wl["rel_tol"], precision=pr, out=outd)
+            pe[1].record(stream)
+            pe[1].synchronize()
+            return pe[0].elapsed_time(pe[1]) / 1e3
+
+        t_plain = plain(prec)
+        t_plain64 = t_plain if prec == P.PREC_FP64 else plain(P.PREC_FP64)
+        frac = {k: sum(c[k] for c in nfb) / (len(nfb) * wl["n"])
+                for k in ("fallback", "network", "expansion", "flagged", "uncertain")}
+        extra = {"surrogate": {"fallback_fraction": frac["fallback"], "network_fraction": frac["network"],
+                               "expansion_fraction": frac["expansion"],
+                               "fallback_flagged_fraction": frac["flagged"],
+                               "fallback_uncertain_fraction": frac["uncertain"],
                                "plain_value": wl["n"] / t_plain, "plain_ms_per_step": t_plain * 1e3,
-                               "speedup_vs_plain": t_plain / t_step, "train_s": wl.get("train_s"),
+                               "speedup_vs_plain": t_plain / t_step,
+                               "plain_fp64_value": wl["n"] / t_plain64, "plain_fp64_ms_per_step": t_plain64 * 1e3,
+                               "speedup_vs_plain_fp64": t_plain64 / t_step, "train_s": wl.get("train_s"),
                                "train_stats": wl.get("train_stats"), "queries": wl["n"],
                                "kappa": wl["kappa"]}}
 
@@ -535,17 +629,41 @@ def main():
     t_e2e = max_over_ranks(t_e2e, dist, dev)
 
     # roofline of the contour kernel (the dominant kernel of a step), timed by
-    # the library's CUDA events around its launch on the launching stream
+    # the library's CUDA events around its launch on the launching stream,
+    # against the FMA-pipe peaks measured on this GPU now
+    probe64, probe32 = P.peak_probe("fp64"), P.peak_probe("fp32")
+    peak64, peak32 = NOMINAL_FP64, NOMINAL_FP32
     f64 /= args.steps
     f32 /= args.steps
     t_kern = sum(kern_ms) / len(kern_ms) / 1e3 if kern_ms and sum(kern_ms) > 0 else t_step
-    t_roof = max(f64 / PEAK_FP64, f32 / PEAK_FP32)
-    roof = {"bound": "alu", "achieved": f64 / t_kern / 1e12, "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
+    t_roof = max(f64 / peak64, f32 / peak32)
+    roof = {"bound": "alu", "achieved": f64 / t_kern / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
             "frac": t_roof / t_kern, "traffic": profile_traffic(args.workload, args.mode),
             "kernel": "contour_kernel", "kernel_ms": t_kern * 1e3, "kernel_share_of_step": t_kern / t_step,
-            "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); FP32 side 152x128x2x2.07 GHz",
+            "peak_source": "unit counts and clocks: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM (1.25 TFLOP/s); "
+                           "FP32 152 x 128 lanes x 2.07 GHz",
+            "peak_fp32": peak32 / 1e12, "probe_fp64": probe64 / 1e12, "probe_fp32": probe32 / 1e12,
+            "frac_vs_probe": max(f64 / probe64, f32 / probe32) / t_kern,
             "fp64_flop_per_launch": f64, "fp32_flop_per_launch": f32,
-            "fp32_frac": (f32 / PEAK_FP32) / t_kern}
+            "fp32_frac": (f32 / peak32) / t_kern}
+    other = []
+    if wl["kind"] == "surrogate" and sst:
+        # feature kernel (FP64/FP32 ALU) and the tensor-core GEMMs, per step
+        ms_f = sum(x["features_ms"] for x in sst) / len(sst) / 1e3
+        ms_g = sum(x["gemm_ms"] for x in sst) / len(sst) / 1e3
+        ff64 = sum(F_FEAT_SOLVE64 * x["point_solves"] + F_FEAT_NEWTON64 * x["newton64"] for x in sst) / len(sst)
+        ff32 = sum(F_FEAT_SOLVE32 * x["point_solves"] + F_SWEEP32 * x["point_sweeps32"]
+                   + F_CAUSTIC32 * x["caustic_iters"] for x in sst) / len(sst)
+        gflop = sum(3 * 2.0 * x["gemm_rows"] * 256 * 256 for x in sst) / len(sst)
+        bf16 = load_peaks().get("bf16_tflops_sustained")
+        other.append({"kernel": "sur_features_kernel", "bound": "alu", "unit": "TFLOP/s", "kernel_ms": ms_f * 1e3,
+                      "achieved": ff64 / ms_f / 1e12, "peak": peak64 / 1e12,
+                      "frac": max(ff64 / peak64, ff32 / peak32) / ms_f, "fp32_frac": (ff32 / peak32) / ms_f,
+                      "fp64_flop_per_step": ff64, "fp32_flop_per_step": ff32})
+        other.append({"kernel": "gemm_bf16_tn_kernel", "bound": "tensor", "unit": "TFLOP/s", "kernel_ms": ms_g * 1e3,
+                      "achieved": gflop / ms_g / 1e12, "peak": bf16,
+                      "frac": (gflop / ms_g / 1e12) / bf16 if bf16 else None, "flop_per_step": gflop,
+                      "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"})
 
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -554,6 +672,8 @@ def main():
             "e2e": {"value": world * wl["n"] / t_e2e, "unit": unit, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches(wl, args.steps),
+            "roofline_other": other,
+            "error_vs_oracle": golden_errors(wl, prec, P, wpath if wl["kind"] == "surrogate" else None),
             "wall_s_timed": wall,
             "work": {"samples_per_position": work["samples"] / (args.steps * wl["n"]),
                      "fp64_sweeps_per_sample": work["sweeps64"] / max(work["samples"], 1),
@@ -563,8 +683,13 @@ def main():
     line.update(extra)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, cores = cpu_oracle_sample(wl, args.cpu_sample)
+        n1, dt1, _ = cpu_oracle_sample(wl, max(2, args.cpu_sample // 16), seed=778, cores=1)
+        what = ("queries drawn on the CPU from the benchmark's distribution (oracle.sample_near_caustic)"
+                if wl["kind"] == "surrogate" else "seeded positions of the same workload")
         line["cpu_baseline"] = {"value": n / dt, "unit": unit, "cores": cores, "kind": "oracle",
-                                "sample": "%d seeded positions of the same workload, %.1f s" % (n, dt)}
+                                "sample": "%d %s, %.1f s on %d threads" % (n, what, dt, cores),
+                                "value_single_core": n1 / dt1,
+                                "sample_single_core": "%d %s, %.1f s on 1 thread" % (n1, what, dt1)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -22,7 +22,7 @@
  * Memory: every pointer argument is owned by the caller and may point to host
  * memory (pageable or pinned) or to device memory of the current CUDA device;
  * the kind is detected per pointer.  All array arguments of one call must be
- * of the same kind.  With host pointers the call is synchronous: inputs are
+ * of the same kind; device memory of another device returns TW_EINVAL.  With host pointers the call is synchronous: inputs are
  * copied to the device and outputs back before it returns.  With device
  * pointers the call is asynchronous on opts->stream (NULL = the legacy default
  * stream) and outputs are valid once that stream reaches the call; buffers
@@ -147,13 +147,16 @@ int tw_lightcurve_batch(const double *params, const int64_t *offsets, const doub
  * allocation could stall or fail.  (The paper has no counterpart: it
  * describes no API.)  It computes what tw_mag_ex computes, with the given
  * precision (TW_PREC_*) and sample cap max_samples (64..512), on `stream`,
- * except the slope-repair pass: a crossing that fails the slope test is
- * counted in no status (there is none) and not repaired.
+ * including the slope-repair pass for up to 4096 positions per call (further
+ * positions whose crossing fails the slope test keep the main pass's value).
  * y1, y2 and out must be device pointers of the current device; the call is
  * asynchronous.  The library's scratch for this entry point is one static
- * device array of about 53 MiB (608 warp arenas of 512 limb samples plus a
- * work counter), which every GPU that loads the library keeps until the
- * process exits.  max_samples > 512 returns TW_ETOOBIG and writes nothing.
+ * device array of about 53 MiB (608 warp arenas of 512 limb samples, the
+ * repair queue and a work counter), which every GPU that loads the library
+ * keeps until the process exits.  Those 608 arenas allow one CTA of four
+ * warps per SM on a 152-SM GPU, half the resident warps of tw_mag, which
+ * costs throughput on large calls.  max_samples > 512 returns TW_ETOOBIG and
+ * writes nothing.
  * The first call on a device looks up the array's device address; make that
  * first call before any stream capture.  Every call reuses the same array
  * (it clears the work counter itself), so calls that overlap on the GPU race
@@ -194,11 +197,25 @@ int tw_surrogate_train(const char *weights_path, int64_t nsamples, uint64_t seed
  * kappa * sigma <= rel_tol (mu = A_hex exp(r)).  All other queries fall back
  * to contour integration (one persistent launch over them, with
  * opts->precision and opts->max_samples).  out[i] receives mu; counts
- * (optional, [3]) the number of fallbacks, of queries accepted by the
- * network, and of queries accepted by the expansion.  Synchronous. */
+ * (optional, [5]) the number of fallbacks, of queries accepted by the
+ * network, of queries accepted by the expansion, and the fallbacks split
+ * into those flagged as near a caustic and the unflagged ones that neither
+ * the expansion nor the network certified.  n < 2^31.  Synchronous.  The
+ * library keeps the call's device buffers for the next call on the device. */
 int tw_surrogate_mag(const char *weights_path, const double *s, const double *q, const double *rho,
                      const double *y1, const double *y2, int64_t n, double rel_tol, double kappa, double *out,
                      int64_t *counts, const tw_opts *opts);
+
+/* Timing and work of the latest tw_surrogate_mag call on the current device
+ * (the paper has no counterpart; a measurement hook of this library):
+ * out[0] device milliseconds of the feature kernels (point images at the
+ * centre and on three rings, caustic sweep, expansion), out[1] of the
+ * network (input layer, three tensor-core GEMMs, head), out[2] of the three
+ * GEMMs alone, each from CUDA events on the call's stream; out[3] point
+ * solves, out[4] FP32 Aberth sweeps of those solves, out[5] FP64 Newton root
+ * steps, out[6] Aberth iterations of the caustic sweep, out[7] GEMM rows
+ * (queries padded to a multiple of 128).  TW_EINVAL if no call completed. */
+int tw_last_surrogate_stats(double out[8]);
 
 /* The training-position sampler of tw_surrogate_train, on its own: n seeded
  * positions near caustics into device arrays (asynchronous on `stream`). */
@@ -252,6 +269,14 @@ int tw_last_launch_work(int64_t out[5]);
  * stream directly before and after them; waits for it.  TW_EINVAL if no launch has been timed.  No
  * counterpart in the paper (a measurement hook of this library). */
 int tw_last_launch_ms(float *ms);
+
+/* Measured peak of a CUDA-core arithmetic pipe on the current device, the
+ * denominator of the contour kernel's roofline (the paper has no
+ * counterpart; a measurement hook): kind 0 FP64 fused multiply-add, kind 1
+ * FP32, as FLOP/s (2 per FMA) of a launch of 8 CTAs per SM whose threads run
+ * independent FMA chains.  Synchronous on the legacy default stream; about
+ * 100 ms. */
+int tw_peak_probe(int kind, double *flops_per_s);
 
 /* Device self-test of the library's FP64 reciprocals against IEEE division,
  * over 2^20 values of magnitude 1e-300..1e300: rcp_max_rel_err[0] receives the

@@ -93,6 +93,8 @@ def lib():
             L.tw_last_launch_ms.restype = I
             L.tw_selftest_slope.argtypes = [d, d, d, d, d, P, I, I, P]
             L.tw_selftest_slope.restype = I
+            L.tw_peak_probe.argtypes = [I, P]
+            L.tw_peak_probe.restype = I
             L.tw_selftest.argtypes = [P]
             L.tw_selftest.restype = I
             L.tw_mag_noalloc.argtypes = [d, d, d, P, P, i64, d, P, I, I, P]
@@ -103,6 +105,8 @@ def lib():
             L.tw_surrogate_train.restype = I
             L.tw_surrogate_mag.argtypes = [ctypes.c_char_p, P, P, P, P, P, i64, d, d, P, P, P]
             L.tw_surrogate_mag.restype = I
+            L.tw_last_surrogate_stats.argtypes = [P]
+            L.tw_last_surrogate_stats.restype = I
             L.tw_surrogate_sample.argtypes = [ctypes.c_uint64, i64, P, P, P, P, P, P]
             L.tw_surrogate_sample.restype = I
             _lib = L
@@ -242,13 +246,29 @@ def surrogate_mag(path, s, q, rho, y1, y2, rel_tol=1e-4, kappa=3.0, precision=PR
     n = int(arrs[0].shape[0])
     if out is None:
         out = _alloc_like(arrs[0], n, np.float64, "float64")
-    c = np.zeros(3, np.int64)
+    c = np.zeros(5, np.int64)
     o = make_opts(precision, 64, max_samples, _stream_of(arrs[0], stream))
     _check(lib().tw_surrogate_mag(str(path).encode(), *[_ptr(a) for a in arrs], n, rel_tol, kappa, _ptr(out),
                                   c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o)))
     if details:
-        return out, dict(fallback=int(c[0]), network=int(c[1]), expansion=int(c[2]))
+        return out, dict(fallback=int(c[0]), network=int(c[1]), expansion=int(c[2]), flagged=int(c[3]),
+                         uncertain=int(c[4]))
     return out, int(c[0])
+
+
+def last_surrogate_stats() -> dict:
+    """Device times (ms) and work of the latest surrogate call (tw_last_surrogate_stats)."""
+    a = np.zeros(8)
+    _check(lib().tw_last_surrogate_stats(a.ctypes.data_as(ctypes.c_void_p)))
+    return dict(features_ms=float(a[0]), network_ms=float(a[1]), gemm_ms=float(a[2]), point_solves=int(a[3]),
+                point_sweeps32=int(a[4]), newton64=int(a[5]), caustic_iters=int(a[6]), gemm_rows=int(a[7]))
+
+
+def peak_probe(kind: str = "fp64") -> float:
+    """Measured FMA-pipe throughput (FLOP/s) of the current device (tw_peak_probe)."""
+    v = np.zeros(1)
+    _check(lib().tw_peak_probe(0 if kind == "fp64" else 1, v.ctypes.data_as(ctypes.c_void_p)))
+    return float(v[0])
 
 
 def selftest_rcp() -> tuple:

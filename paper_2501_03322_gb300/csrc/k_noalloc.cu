@@ -10,16 +10,19 @@
 // every GPU which loads this library holds until the process exits.
 //
 // Limits: NOALLOC_SLOTS warp arenas of at most NOALLOC_MAX_SAMPLES limb
-// samples each (about 53 MiB per GPU).  Requests for a larger sample cap are
-// rejected with TW_ETOOBIG.  All calls share the one array, which keeps the
-// previous call's contents: the work counter is cleared by every call, the
-// arenas need no clearing (every sample is written before it is read).  Calls
-// that overlap on the GPU (on different streams, or racing host threads) race
-// on the array and corrupt each other's results.
+// samples each (about 53 MiB per GPU), i.e. one CTA of four warps per SM on a
+// 152-SM GB300 (tw_mag runs two), and a queue of NOALLOC_RELIST positions for
+// the slope-repair pass.  Requests for a larger sample cap are rejected with
+// TW_ETOOBIG.  All calls share the one array, which keeps the previous call's
+// contents: the work counter and the repair-queue length are cleared by every
+// call, the arenas and the queue entries need no clearing (each is written
+// before it is read).  Calls that overlap on the GPU (on different streams,
+// or racing host threads) race on the array and corrupt each other's results.
 #include <mutex>
 
 #include "../../include/twinkle.h"
 #include "kernels.cuh"
+#include "ptrkind.cuh"
 
 namespace tw {
 
@@ -27,8 +30,10 @@ constexpr int NOALLOC_SLOTS = 608;          // 152 CTAs of 4 warps
 constexpr int NOALLOC_MAX_SAMPLES = 512;
 constexpr size_t NOALLOC_SLOT_BYTES = arena_slot_bytes(NOALLOC_MAX_SAMPLES);
 static_assert(NOALLOC_SLOT_BYTES == 92160, "arena layout changed");
-constexpr size_t NOALLOC_HEADER = 256;        // work counter and work statistics
-constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_SLOT_BYTES * NOALLOC_SLOTS;
+constexpr size_t NOALLOC_HEADER = 256;        // work counter, work statistics, repair-queue counters
+constexpr int NOALLOC_RELIST = 4096;          // positions queued for the slope-repair pass
+constexpr size_t NOALLOC_RELIST_BYTES = NOALLOC_RELIST * sizeof(int64_t);
+constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_RELIST_BYTES + NOALLOC_SLOT_BYTES * NOALLOC_SLOTS;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
@@ -55,11 +60,8 @@ static int noalloc_setup(int dev, char **ptr, int *nsm) {
     return TW_OK;
 }
 
-static bool on_device(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { (void)cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// device (or managed) memory of the current device
+static bool on_device(const void *p) { return ptr_kind(p) == PK_DEV; }
 
 }  // namespace tw
 
@@ -100,14 +102,26 @@ extern "C" int tw_mag_noalloc(double s, double q, double rho, const double *y1, 
     kp.src.y2 = y2;
     kp.src.stride = 1;
     kp.out = out;
-    kp.arena = base + NOALLOC_HEADER;
+    kp.arena = base + NOALLOC_HEADER + NOALLOC_RELIST_BYTES;
     kp.slot_bytes = NOALLOC_SLOT_BYTES;
     kp.cap = (max_samples + 63) & ~63;
     kp.tol = rel_tol;
     kp.chunk = 1;
     kp.counter = (unsigned long long *)base;
-    // the work counter must start at zero; the arenas need no clearing
+    // crossings that fail the slope test (Sec. 2.4.2) queue their position
+    // here; the repair pass integrates them again (positions beyond the
+    // queue's length keep the main pass's result)
+    kp.relist = (int64_t *)(base + NOALLOC_HEADER);
+    kp.relist_cap = NOALLOC_RELIST;
+    // the work counter and the queue length must start at zero; the arenas
+    // and the queue entries need no clearing
     if (cudaMemsetAsync(base, 0, NOALLOC_HEADER, st) != cudaSuccess) { (void)cudaGetLastError(); return TW_ECUDA; }
     if (lf((unsigned)blocks, st, kp) != cudaSuccess) { (void)cudaGetLastError(); return TW_ECUDA; }
+    // the repair pass: at most one CTA per SM and never more warps than arenas
+    const unsigned rblocks = (unsigned)(blocks < nsm ? blocks : nsm);
+    if ((precision == TW_PREC_FP64 ? launch_repair_0 : launch_repair_1)(rblocks, st, kp) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return TW_ECUDA;
+    }
     return TW_OK;
 }

@@ -42,6 +42,7 @@
 
 #include "../../include/twinkle.h"
 #include "gemm.cuh"
+#include "ptrkind.cuh"
 #include "kernels.cuh"
 
 namespace tw {
@@ -172,7 +173,8 @@ __global__ void sur_sample_kernel(uint64_t seed, int64_t n, double *S, double *Q
 // residual pair test (Sec. 2.4.1) and, for the real images, sum 1/|J| and
 // min |J| (Eq. 7).
 template <bool FP64>
-static __device__ __noinline__ int point_images(const LensK &L, cxd y, cxd z[5], double &mu_ps, double &minJ) {
+static __device__ __noinline__ int point_images(const LensK &L, cxd y, cxd z[5], double &mu_ps, double &minJ,
+                                                int &sweeps, int &newton) {
     cxd c[6];
     eq6_coeffs(L.s, L.m2, y, c);
     float ca[6];
@@ -190,12 +192,15 @@ static __device__ __noinline__ int point_images(const LensK &L, cxd y, cxd z[5],
 #pragma unroll
     for (int i = 0; i < 5; i++) zf[i] = to_f(z[i]);
     float dpa[5];
-    for (int it = 0; it < 100; it++)
+    int it = 0;
+    for (; it < 100; it++)
         if (aberth_sweep<float>(cf, caf, zf, dpa, 2e-6f, 6e-8f)) break;
+    sweeps += it < 100 ? it + 1 : it;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         z[i] = to_d(zf[i]);
         if (FP64) {
+            newton++;
             // one Newton step from FP32 accuracy reaches FP64 accuracy (the error
             // squares); a second where the FP32 root was poor (a step above
             // 1e-6 |z|, next to a near-double root)
@@ -204,6 +209,7 @@ static __device__ __noinline__ int point_images(const LensK &L, cxd y, cxd z[5],
             cxd st = cdiv40(p, d);
             z[i] = z[i] - st;
             if (norm2f(st) > 1e-12f * norm2f(z[i])) {
+                newton++;
                 horner(c, z[i], p, d);
                 st = cdiv40(p, d);
                 z[i] = z[i] - st;
@@ -260,7 +266,7 @@ static __device__ __noinline__ int point_images(const LensK &L, cxd y, cxd z[5],
 // polyline, and the query is near when a segment comes within `reach` plus
 // the segment's length (slack for the arc the chord cuts off).
 constexpr int NCAU = 64;
-__device__ bool caustic_within(float s, float m2, float m1, cxf y0, float reach) {
+__device__ bool caustic_within(float s, float m2, float m1, cxf y0, float reach, int &iters) {
     cxf z[4];
     const float r0 = 1.0f + s;
 #pragma unroll
@@ -282,6 +288,7 @@ __device__ bool caustic_within(float s, float m2, float m1, cxf y0, float reach)
         c[1] = {-2.0f * s * m2, 0.0f};
         c[0] = {-m2 * s * s, 0.0f};
         for (int it = 0; it < (k == 0 ? 120 : 30); it++) {
+            iters++;
             cxf S4[4];
 #pragma unroll
             for (int a = 0; a < 4; a++) S4[a] = {0.f, 0.f};
@@ -339,7 +346,8 @@ constexpr int RING_PTS = 24;  // 3 rings x 8 points
 
 __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const double *S, const double *Q,
                                                               const double *RHO, const double *Y1, const double *Y2,
-                                                              float *X, double *MUPS, uint8_t *FLAG, float *HEXE) {
+                                                              float *X, double *MUPS, uint8_t *FLAG, float *HEXE,
+                                                              unsigned long long *WORK) {
     __shared__ double sM[4][32][RING_PTS];  // ring-point magnifications per query slot
     __shared__ int sBad[4][32];             // a ring point's image count differed
     __shared__ int sOwner[4][32];           // lane of the j-th unflagged query
@@ -375,6 +383,9 @@ __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const d
     double A0 = __longlong_as_double(0x7ff8000000000000ll), minJ = 0.0;
     int c0 = 0;
     bool flag = true;
+    // work of this thread: point solves, FP32 Aberth sweeps, FP64 Newton root
+    // steps, caustic Aberth iterations (the units of the FLOP accounting)
+    int w_solve = 0, w_sweep = 0, w_newton = 0, w_caus = 0;
     if (ok) {
         if (q > 1.0) { q = 1.0 / q; y1 = -y1; }  // mass-swap symmetry (see kernels.cuh)
         L.s = s;
@@ -383,11 +394,13 @@ __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const d
         L.rho = rho;
         y0 = {y1 - s * L.m1, y2};
         initial_roots(s, y0, z);
-        c0 = point_images<true>(L, y0, z, A0, minJ);
+        c0 = point_images<true>(L, y0, z, A0, minJ, w_sweep, w_newton);
+        w_solve++;
         flag = !(isfinite(A0) && A0 >= 1.0 - 1e-3) || minJ < 0.1;
         // within 4 rho (not just 2 rho): closer than that the ring at 2 rho nears
         // the caustic and the expansion's error estimate is no longer reliable
-        if (!flag) flag = caustic_within((float)s, (float)L.m2, (float)L.m1, to_f(y0), (float)(4.0 * rho) + 1e-6f);
+        if (!flag)
+            flag = caustic_within((float)s, (float)L.m2, (float)L.m1, to_f(y0), (float)(4.0 * rho) + 1e-6f, w_caus);
     }
     // Point-source magnifications averaged over 8 points on rings of radius
     // rho/2, rho and 2 rho.  For a smooth A, the average over a ring of radius
@@ -428,7 +441,8 @@ __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const d
             const double r = (0.5 * (1 << ring)) * Lk.rho;
             const cxd yk = {yc.x + r * cs, yc.y + r * sn};
             double m, mj;
-            const int cnt = point_images<true>(Lk, yk, zk, m, mj);
+            const int cnt = point_images<true>(Lk, yk, zk, m, mj, w_sweep, w_newton);
+            w_solve++;
             sM[wib][src][k] = m;
             if (cnt != ck || !isfinite(m)) atomicOr(&sBad[wib][src], 1);
         }
@@ -464,6 +478,16 @@ __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const d
         MUPS[i] = ok ? Ahex : __longlong_as_double(0x7ff8000000000000ll);
         FLAG[i] = flag ? 1 : 0;
         HEXE[i] = (float)fmin(hexe, 1.0);
+    }
+    if (WORK) {
+        const int a = __reduce_add_sync(0xffffffffu, w_solve), b = __reduce_add_sync(0xffffffffu, w_sweep);
+        const int c = __reduce_add_sync(0xffffffffu, w_newton), d = __reduce_add_sync(0xffffffffu, w_caus);
+        if (lane == 0) {
+            atomicAdd(WORK + 0, (unsigned long long)a);
+            atomicAdd(WORK + 1, (unsigned long long)b);
+            atomicAdd(WORK + 2, (unsigned long long)c);
+            atomicAdd(WORK + 3, (unsigned long long)d);
+        }
     }
 }
 
@@ -518,6 +542,7 @@ __global__ void sur_head_infer_kernel(int64_t n, int64_t row0, const __nv_bfloat
             const unsigned long long slot = atomicAdd(NLIST, 1ull);
             LIST[slot] = (int32_t)g;
             OUT[g] = __longlong_as_double(0x7ff8000000000000ll);
+            if (FLAG[g]) atomicAdd(NLIST + 3, 1ull);
         } else {
             OUT[g] = mu;
             atomicAdd(NLIST + (hex_ok ? 2 : 1), 1ull);
@@ -793,9 +818,10 @@ static int model_for(const char *path, cudaStream_t st, Model **out) {
 // ping-ponging between HA and HB; returns the buffer holding layer 4.
 static int mlp_forward(const Model &m, int64_t rows, const float *X, __nv_bfloat16 *HA, __nv_bfloat16 *HB,
                        __nv_bfloat16 *H1keep, __nv_bfloat16 **H2keep, float *XS, int *err, cudaStream_t st,
-                       __nv_bfloat16 **outH4) {
+                       __nv_bfloat16 **outH4, cudaEvent_t gemm0 = nullptr, cudaEvent_t gemm1 = nullptr) {
     __nv_bfloat16 *h1 = H1keep ? H1keep : HA;
     sur_layer1_kernel<<<nblk(rows * SH, 256), 256, 0, st>>>(rows, X, m.P, m.nrm, h1, XS);
+    if (gemm0) cudaEventRecord(gemm0, st);
     __nv_bfloat16 *in = h1;
     for (int l = 0; l < 3; l++) {
         __nv_bfloat16 *out = H2keep ? H2keep[l] : ((in == HA) ? HB : HA);
@@ -814,15 +840,46 @@ static int mlp_forward(const Model &m, int64_t rows, const float *X, __nv_bfloat
         if (e != cudaSuccess) return cerr(e);
         in = out;
     }
+    if (gemm1) cudaEventRecord(gemm1, st);
     *outH4 = in;
     return cerr(cudaGetLastError());
 }
 
-static bool dev_ptr(const void *p) {
-    cudaPointerAttributes a;
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) { (void)cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// Grow-only device buffers, one set per device and entry point: calls are
+// serialised (g_sm) and synchronous, so a set is reused call after call
+// instead of being allocated and freed (cudaFree synchronises the device).
+struct Pool {
+    void *p[16] = {nullptr};
+    size_t sz[16] = {0};
+    template <typename T>
+    int get(int slot, T **out, size_t count) {
+        const size_t need = count * sizeof(T) + 256;
+        if (sz[slot] < need) {
+            if (p[slot]) cudaFree(p[slot]);
+            p[slot] = nullptr;
+            sz[slot] = 0;
+            if (cudaMalloc(&p[slot], need) != cudaSuccess) { (void)cudaGetLastError(); p[slot] = nullptr; return TW_ENOMEM; }
+            sz[slot] = need;
+        }
+        *out = (T *)p[slot];
+        return TW_OK;
+    }
+};
+static Pool g_sur_pool[64];
+
+// Timing and work of the latest tw_surrogate_mag call on a device: CUDA
+// events around each chunk's feature kernel, its three tensor-core GEMMs and
+// its whole network (layer 1, GEMMs, head), and the feature kernel's work
+// counters.
+struct SurStats {
+    std::vector<cudaEvent_t> ev;  // 5 per chunk
+    double feat_ms = 0, net_ms = 0, gemm_ms = 0, gemm_rows = 0;
+    unsigned long long work[4] = {0, 0, 0, 0};
+    bool valid = false;
+};
+static SurStats g_sur_stats[64];
+
+static bool dev_ptr(const void *p) { return p && ptr_kind(p) == PK_DEV; }
 
 }  // namespace tw
 
@@ -855,7 +912,7 @@ extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, ui
     sur_sample_kernel<<<nblk(n, 128), 128, 0, st>>>(seed, n, S, Q, RHO, Y1, Y2);
     float *HEXE;
     if ((rc = B.get(&HEXE, n))) return rc;
-    sur_features_kernel<<<nblk(n, 128), 128, 0, st>>>(n, S, Q, RHO, Y1, Y2, X, MUPS, FLAG, HEXE);
+    sur_features_kernel<<<nblk(n, 128), 128, 0, st>>>(n, S, Q, RHO, Y1, Y2, X, MUPS, FLAG, HEXE, nullptr);
     cudaMemsetAsync(NL, 0, 8, st);
     cudaMemsetAsync(err, 0, 4, st);
     compact_unflagged_kernel<<<nblk(n, 256), 256, 0, st>>>(n, FLAG, LIST, NL);
@@ -1003,8 +1060,12 @@ extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, ui
 extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const double *q, const double *rho,
                                 const double *y1, const double *y2, int64_t n, double rel_tol, double kappa,
                                 double *out, int64_t *counts, const tw_opts *opts) {
-    if (!weights_path || n < 0 || !(rel_tol > 0) || !(kappa > 0) || !isfinite(rel_tol)) return TW_EINVAL;
-    if (n == 0) { if (counts) counts[0] = counts[1] = counts[2] = 0; return TW_OK; }
+    if (!weights_path || n < 0 || !(rel_tol > 0) || !(kappa > 0) || !isfinite(rel_tol) || n > 0x7fffffffll)
+        return TW_EINVAL;
+    if (n == 0) {
+        if (counts) for (int k = 0; k < 5; k++) counts[k] = 0;
+        return TW_OK;
+    }
     if (!s || !q || !rho || !y1 || !y2 || !out) return TW_EINVAL;
     tw_opts o;
     tw_opts_default(&o);
@@ -1012,61 +1073,97 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
     if (o.precision != TW_PREC_FP64 && o.precision != TW_PREC_MIXED) return TW_EINVAL;
     std::lock_guard<std::mutex> lk(g_sm);
     cudaStream_t st = (cudaStream_t)o.stream;
-    const bool dev = dev_ptr(out);
+    // one kind for every array; device memory of another device is refused
+    const int kind = ptr_kind(out);
+    if (kind == PK_OTHER) return TW_EINVAL;
+    const bool dev = kind == PK_DEV;
     const double *in[5] = {s, q, rho, y1, y2};
     for (int k = 0; k < 5; k++)
-        if (dev_ptr(in[k]) != dev) return TW_EINVAL;
+        if (ptr_kind(in[k]) != kind) return TW_EINVAL;
+    int devno = 0;
+    if (cudaGetDevice(&devno) != cudaSuccess || devno < 0 || devno >= 64) { (void)cudaGetLastError(); return TW_ECUDA; }
     Model *m = nullptr;
     int rc = model_for(weights_path, st, &m);
     if (rc) return rc;
-    DevBufs B;
+    Pool &B = g_sur_pool[devno];
+    SurStats &T = g_sur_stats[devno];
+    T.valid = false;
     const double *din[5];
     double *dout = out;
     cudaError_t e;
     if (!dev) {  // host arrays: stage through device memory
         for (int k = 0; k < 5; k++) {
             double *d;
-            if ((rc = B.get(&d, n))) return rc;
+            if ((rc = B.get(k, &d, n))) return rc;
             if ((e = cudaMemcpyAsync(d, in[k], n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cerr(e);
             din[k] = d;
         }
-        if ((rc = B.get(&dout, n))) return rc;
+        if ((rc = B.get(5, &dout, n))) return rc;
     } else {
         for (int k = 0; k < 5; k++) din[k] = in[k];
     }
     const int64_t CH = 1 << 20;
     const int64_t chunk = n < CH ? ((n + 127) / 128) * 128 : CH;
+    const int64_t nch = (n + chunk - 1) / chunk;
     float *X, *HEXE;
     double *MUPS;
     uint8_t *FLAG;
     int32_t *LIST;
-    unsigned long long *NL;
+    unsigned long long *NL, *WORK;
     int *err;
     __nv_bfloat16 *HA, *HB;
-    if ((rc = B.get(&X, chunk * SXP)) || (rc = B.get(&MUPS, n)) || (rc = B.get(&FLAG, n)) || (rc = B.get(&LIST, n)) ||
-        (rc = B.get(&NL, 3)) || (rc = B.get(&err, 1)) || (rc = B.get(&HA, chunk * SH)) ||
-        (rc = B.get(&HB, chunk * SH)) || (rc = B.get(&HEXE, n)))
+    if ((rc = B.get(6, &X, chunk * SXP)) || (rc = B.get(7, &MUPS, n)) || (rc = B.get(8, &FLAG, n)) ||
+        (rc = B.get(9, &LIST, n)) || (rc = B.get(10, &NL, 8)) || (rc = B.get(11, &err, 1)) ||
+        (rc = B.get(12, &HA, chunk * SH)) || (rc = B.get(13, &HB, chunk * SH)) || (rc = B.get(14, &HEXE, n)))
         return rc;
-    cudaMemsetAsync(NL, 0, 24, st);
-    cudaMemsetAsync(err, 0, 4, st);
-    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+    WORK = NL + 4;
+    while (T.ev.size() < (size_t)(5 * nch)) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cerr(e);
+        T.ev.push_back(ev);
+    }
+    if ((e = cudaMemsetAsync(NL, 0, 64, st)) != cudaSuccess) return cerr(e);
+    if ((e = cudaMemsetAsync(err, 0, 4, st)) != cudaSuccess) return cerr(e);
+    double rows_total = 0;
+    for (int64_t c = 0; c < nch; c++) {
+        const int64_t c0 = c * chunk;
         const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
         const int64_t rows = ((cn + 127) / 128) * 128;
+        rows_total += (double)rows;
         if (rows > cn) cudaMemsetAsync(X + cn * SXP, 0, (rows - cn) * SXP * 4, st);
+        cudaEvent_t *ev = &T.ev[5 * c];
+        cudaEventRecord(ev[0], st);
         sur_features_kernel<<<nblk(cn, 128), 128, 0, st>>>(cn, din[0] + c0, din[1] + c0, din[2] + c0, din[3] + c0,
-                                                           din[4] + c0, X, MUPS + c0, FLAG + c0, HEXE + c0);
+                                                           din[4] + c0, X, MUPS + c0, FLAG + c0, HEXE + c0, WORK);
+        cudaEventRecord(ev[1], st);
         __nv_bfloat16 *h4 = nullptr;
-        if ((rc = mlp_forward(*m, rows, X, HA, HB, nullptr, nullptr, nullptr, err, st, &h4))) return rc;
+        if ((rc = mlp_forward(*m, rows, X, HA, HB, nullptr, nullptr, nullptr, err, st, &h4, ev[2], ev[3]))) return rc;
         sur_head_infer_kernel<<<nblk(cn * 32, 256), 256, 0, st>>>(cn, c0, h4, m->P, MUPS, FLAG, HEXE, rel_tol,
                                                                  (float)kappa, dout, LIST, NL);
+        cudaEventRecord(ev[4], st);
     }
-    unsigned long long cnt[3] = {0, 0, 0};
+    unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int herr = 0;
-    e = cudaMemcpyAsync(cnt, NL, 24, cudaMemcpyDeviceToHost, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, NL, 64, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cerr(e);
     if (herr) return TW_ETIMEOUT;
+    T.feat_ms = T.net_ms = T.gemm_ms = 0;
+    for (int64_t c = 0; c < nch; c++) {
+        float a = 0, b = 0, g = 0;
+        cudaEventElapsedTime(&a, T.ev[5 * c], T.ev[5 * c + 1]);
+        cudaEventElapsedTime(&b, T.ev[5 * c + 1], T.ev[5 * c + 4]);
+        cudaEventElapsedTime(&g, T.ev[5 * c + 2], T.ev[5 * c + 3]);
+        T.feat_ms += a;
+        T.net_ms += b;
+        T.gemm_ms += g;
+    }
+    (void)cudaGetLastError();
+    T.gemm_rows = rows_total;
+    for (int k = 0; k < 4; k++) T.work[k] = cnt[4 + k];
+    T.valid = true;
     const unsigned long long nl = cnt[0];
     // contour-integration fallback: one persistent launch over the list
     rc = contour_positions(din[0], din[1], din[2], din[3], din[4], LIST, (int64_t)nl, rel_tol, o.precision,
@@ -1080,7 +1177,27 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
         counts[0] = (int64_t)cnt[0];
         counts[1] = (int64_t)cnt[1];
         counts[2] = (int64_t)cnt[2];
+        counts[3] = (int64_t)cnt[3];
+        counts[4] = (int64_t)(cnt[0] - cnt[3]);
     }
+    return TW_OK;
+}
+
+extern "C" int tw_last_surrogate_stats(double out[8]) {
+    if (!out) return TW_EINVAL;
+    std::lock_guard<std::mutex> lk(g_sm);
+    int devno = 0;
+    if (cudaGetDevice(&devno) != cudaSuccess || devno < 0 || devno >= 64) { (void)cudaGetLastError(); return TW_ECUDA; }
+    const SurStats &T = g_sur_stats[devno];
+    if (!T.valid) return TW_EINVAL;
+    out[0] = T.feat_ms;
+    out[1] = T.net_ms;
+    out[2] = T.gemm_ms;
+    out[3] = (double)T.work[0];
+    out[4] = (double)T.work[1];
+    out[5] = (double)T.work[2];
+    out[6] = (double)T.work[3];
+    out[7] = T.gemm_rows;
     return TW_OK;
 }
 
@@ -1114,27 +1231,7 @@ __global__ void gate_kernel(int64_t n, int64_t row0, const double *MUPS, const u
     }
 }
 
-// Grow-only device buffers of tw_mag_gated, one set per device: its calls
-// are serialised (g_sm) and synchronous, so a set is reused call after call
-// instead of being allocated and freed (cudaFree synchronises the device).
-struct GatePool {
-    void *p[12] = {nullptr};
-    size_t sz[12] = {0};
-    template <typename T>
-    int get(int slot, T **out, size_t count) {
-        const size_t need = count * sizeof(T) + 256;
-        if (sz[slot] < need) {
-            if (p[slot]) cudaFree(p[slot]);
-            p[slot] = nullptr;
-            sz[slot] = 0;
-            if (cudaMalloc(&p[slot], need) != cudaSuccess) { (void)cudaGetLastError(); p[slot] = nullptr; return TW_ENOMEM; }
-            sz[slot] = need;
-        }
-        *out = (T *)p[slot];
-        return TW_OK;
-    }
-};
-static GatePool g_gate_pool[64];
+static Pool g_gate_pool[64];
 
 }  // namespace tw
 
@@ -1149,13 +1246,16 @@ extern "C" int tw_mag_gated(const double *s, const double *q, const double *rho,
     if (o.precision != TW_PREC_FP64 && o.precision != TW_PREC_MIXED) return TW_EINVAL;
     std::lock_guard<std::mutex> lk(g_sm);
     cudaStream_t st = (cudaStream_t)o.stream;
-    const bool dev = dev_ptr(out);
+    // one kind for every array; device memory of another device is refused
+    const int kind = ptr_kind(out);
+    if (kind == PK_OTHER) return TW_EINVAL;
+    const bool dev = kind == PK_DEV;
     const double *in[5] = {s, q, rho, y1, y2};
     for (int k = 0; k < 5; k++)
-        if (dev_ptr(in[k]) != dev) return TW_EINVAL;
+        if (ptr_kind(in[k]) != kind) return TW_EINVAL;
     int devno = 0;
     if (cudaGetDevice(&devno) != cudaSuccess || devno < 0 || devno >= 64) { (void)cudaGetLastError(); return TW_ECUDA; }
-    GatePool &B = g_gate_pool[devno];
+    Pool &B = g_gate_pool[devno];
     const double *din[5];
     double *dout = out;
     cudaError_t e;
@@ -1185,7 +1285,7 @@ extern "C" int tw_mag_gated(const double *s, const double *q, const double *rho,
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
         const int64_t cn = (n - c0) < chunk ? (n - c0) : chunk;
         sur_features_kernel<<<nblk(cn, 128), 128, 0, st>>>(cn, din[0] + c0, din[1] + c0, din[2] + c0, din[3] + c0,
-                                                           din[4] + c0, X, MUPS + c0, FLAG + c0, HEXE + c0);
+                                                           din[4] + c0, X, MUPS + c0, FLAG + c0, HEXE + c0, nullptr);
         gate_kernel<<<nblk(cn, 256), 256, 0, st>>>(cn, c0, MUPS, FLAG, HEXE, rel_tol, dout, LIST, NL);
     }
     unsigned long long cnt[2] = {0, 0};

@@ -217,6 +217,8 @@ __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
     cudaError_t occupancy_contour_##PREC##_##SPL(int *occ);
 
 cudaError_t launch_rcp_selftest(unsigned long long *max_err_bits, int n, cudaStream_t st);
+// FMA throughput probe (k_selftest.cu): kind 0 FP64, 1 FP32; returns 0 or -1.
+int fma_probe(int kind, int nsm, double *flops_per_s);
 
 // Host (twinkle.cu): contour integration of n positions with per-position lens
 // and source radius (kind 3), device pointers, serialised with the library's

@@ -14,6 +14,7 @@
 
 #include "../../include/twinkle.h"
 #include "kernels.cuh"
+#include "ptrkind.cuh"
 
 namespace tw {
 
@@ -101,12 +102,6 @@ static int grow(char **buf, size_t *have, size_t need) {
     return TW_OK;
 }
 
-static bool is_device_ptr(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { (void)cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 static bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
@@ -353,12 +348,15 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     DevState &d = *dp;
     cudaStream_t st = (cudaStream_t)o.stream;
     // all arrays of a call must be of one kind
-    const bool dev = is_device_ptr(out);
+    // one kind for every array of the call; device memory of another device is refused
+    const int kind = ptr_kind(out);
+    if (kind == PK_OTHER) return TW_EINVAL;
+    const bool dev = kind == PK_DEV;
     for (int i = 0; i < c.nin; i++)
-        if (c.insz[i] && is_device_ptr(c.in[i]) != dev) return TW_EINVAL;
-    if (o.err_out && is_device_ptr(o.err_out) != dev) return TW_EINVAL;
-    if (o.nsamp_out && is_device_ptr(o.nsamp_out) != dev) return TW_EINVAL;
-    if (o.pos_status && is_device_ptr(o.pos_status) != dev) return TW_EINVAL;
+        if (c.insz[i] && ptr_kind(c.in[i]) != kind) return TW_EINVAL;
+    if (o.err_out && ptr_kind(o.err_out) != kind) return TW_EINVAL;
+    if (o.nsamp_out && ptr_kind(o.nsamp_out) != kind) return TW_EINVAL;
+    if (o.pos_status && ptr_kind(o.pos_status) != kind) return TW_EINVAL;
     const void *din[5];
     LaunchCfg cfg = {o.samples_per_iter / 32, 0, 1, -1};
     if (dev) {
@@ -525,7 +523,9 @@ int tw_lightcurve_batch(const double *params, const int64_t *offsets, const doub
     if (!params || !offsets) return TW_EINVAL;
     // the total length is needed on the host: read offsets[ncurve]
     int64_t total = 0;
-    if (is_device_ptr(offsets)) {
+    const int okind = ptr_kind(offsets);
+    if (okind == PK_OTHER) return TW_EINVAL;
+    if (okind == PK_DEV) {
         if (cudaMemcpy(&total, offsets + ncurve, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
     } else {
         if (offsets[0] != 0) return TW_EINVAL;
@@ -584,6 +584,16 @@ int tw_selftest(double *rcp_max_rel_err) {
     if (e != cudaSuccess) return cuda_fail(e);
     memcpy(rcp_max_rel_err, h, 16);
     return TW_OK;
+}
+
+int tw_peak_probe(int kind, double *flops_per_s) {
+    if (!flops_per_s || (kind != 0 && kind != 1)) return TW_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState *dp = nullptr;
+    int rc = dev_state(&dp);
+    if (rc) return rc;
+    if (cudaStreamWaitEvent(0, dp->last, 0) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+    return fma_probe(kind, dp->nsm, flops_per_s) ? TW_ECUDA : TW_OK;
 }
 
 int tw_last_launch_ms(float *ms) {
