@@ -8,12 +8,18 @@ arithmetic).  Run from the repository root:
 
 Files (text, one position per line: inputs, mu, oracle status):
   lightcurve_central.txt  all 1000 points of the central-caustic light curve
-  map_planetary.txt       256 sampled cells of the 512 x 512 planetary-caustic map
+  map_planetary.txt       256 sampled cells of the 512 x 512 planetary-caustic map, plus 96
+                          cells whose limb passes within rho of the caustic (most cross it)
   stress_resonant.txt     200 sampled positions of the resonant large-source set
-  batch_lightcurves.txt   192 sampled (curve, time) points of the 4096-curve batch
+  stress_resonant_1e4.txt the first 10^4 positions of the resonant large-source set
+  batch_lightcurves.txt   192 sampled (curve, time) points of the 4096-curve batch, plus 80
+                          points (one per curve) whose limb passes within rho of the caustic
   paper_worked.txt        the paper's worked configurations (Fig. 1, 2, 5)
-  surrogate_queries.txt   192 positions near the caustics of 8 lenses of the surrogate's range
+  surrogate_queries.txt   1024 positions near the caustics of 64 lenses of the surrogate's range
   central_wide.txt        4096 centres on the central caustic of a wide planetary lens
+
+Positions "near the caustic" are chosen with the oracle's caustic (nearest of
+its sampled points within rho of the limb's centre).
 """
 from __future__ import annotations
 
@@ -54,13 +60,28 @@ def lightcurve_central():
     _write("lightcurve_central.txt", hdr, ["t", "mu", "status", "ncross"], zip(t, mu, st, nx))
 
 
+def _near_caustic(points, s, q, rho, M=8192):
+    """Mask of points within rho of the oracle's caustic (sampled at M angles)."""
+    from scipy.spatial import cKDTree
+
+    _, cc = O.caustic(s, q, M)
+    c = cc.ravel()
+    d, _ = cKDTree(np.c_[c.real, c.imag]).query(points)
+    return d < rho
+
+
 def map_planetary():
     c = W.MAP_PLANETARY
     y1, y2 = W.map_grid()
     idx = W.sample_indices(y1.size, 256, seed=101)
+    near = np.nonzero(_near_caustic(np.c_[y1, y2], c["s"], c["q"], c["rho"]))[0]
+    near = np.setdiff1d(near, idx)
+    extra = np.sort(np.random.default_rng(102).choice(near, size=min(96, near.size), replace=False))
+    idx = np.r_[idx, extra]
     mu, st, nx = O.mag(c["s"], c["q"], c["rho"], y1[idx], y2[idx], scan_K=256)
     hdr = ("Planetary-caustic map: s=0.8, q=1e-4, rho=5e-4, 512x512 cell centres of the 0.1x0.1 box centred\n"
-           "on (-0.44985, 0.016993); 256 cells sampled with seed 101; oracle magnifications.")
+           "on (-0.44985, 0.016993); 256 cells sampled with seed 101, then 96 cells (seed 102) among those within\n"
+           "rho of the oracle's caustic; oracle magnifications.")
     _write("map_planetary.txt", hdr, ["index", "y1", "y2", "mu", "status", "ncross"], zip(idx, y1[idx], y2[idx], mu, st, nx))
 
 
@@ -72,6 +93,17 @@ def stress_resonant():
     hdr = ("Resonant large source: s=1, q=0.5, rho=0.05, 1e6 positions uniform in |y|<0.6 (seed 2);\n"
            "200 sampled with seed 202; oracle magnifications.")
     _write("stress_resonant.txt", hdr, ["index", "y1", "y2", "mu", "status", "ncross"], zip(idx, y1[idx], y2[idx], mu, st, nx))
+
+
+def stress_resonant_1e4():
+    c = W.STRESS_RESONANT
+    y1, y2 = W.stress_positions()
+    idx = np.arange(10000)
+    mu, st, nx = O.mag(c["s"], c["q"], c["rho"], y1[idx], y2[idx], scan_K=256, nthreads=os.cpu_count())
+    hdr = ("Resonant large source: s=1, q=0.5, rho=0.05, 1e6 positions uniform in |y|<0.6 (seed 2);\n"
+           "the first 10^4 positions; oracle magnifications.")
+    _write("stress_resonant_1e4.txt", hdr, ["index", "y1", "y2", "mu", "status", "ncross"],
+           zip(idx, y1[idx], y2[idx], mu, st, nx))
 
 
 def batch_lightcurves():
@@ -90,12 +122,32 @@ def batch_lightcurves():
         mu, st, nx = O.lightcurve(s, q, rho, u0, alpha, t0, tE, times[pick], scan_K=256, nthreads=1)
         return [(k, i, times[i], m, a, b) for i, m, a, b in zip(pick, mu, st, nx)]
 
+    def near(k):
+        """One time of curve k whose limb centre lies within rho of the caustic, or None."""
+        s, q, rho, u0, alpha, t0, tE = params[k]
+        t = times[offsets[k]:offsets[k + 1]]
+        y1, y2 = O.trajectory(u0, alpha, t0, tE, t)
+        m = np.nonzero(_near_caustic(np.c_[y1, y2], s, q, rho, M=2048))[0]
+        if m.size == 0:
+            return None
+        return (k, np.array([offsets[k] + m[np.random.default_rng(int(k)).integers(m.size)]]))
+
+    order = np.random.default_rng(304).permutation(params.shape[0])
+    crossing = []
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
+        for start in range(0, order.size, 64):
+            crossing += [j for j in ex.map(near, order[start:start + 64]) if j is not None]
+            if len(crossing) >= 80:
+                break
+    jobs += sorted(crossing[:80], key=lambda j: j[0])
+
     rows = []
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
         for r in ex.map(run, jobs):
             rows.extend(r)
     hdr = ("Batch of 4096 light curves (workloads.batch_lightcurves, seed 0); 64 curves x 3 times sampled\n"
-           "with seed 303; oracle magnifications.")
+           "with seed 303, then one time on each of 80 curves (curve order seed 304) whose limb centre lies\n"
+           "within rho of the oracle's caustic; oracle magnifications.")
     _write("batch_lightcurves.txt", hdr, ["curve", "index", "t", "mu", "status", "ncross"], rows)
 
 
@@ -134,20 +186,20 @@ def paper_worked():
 
 
 def surrogate_queries():
-    """Query positions near caustics for the surrogate path: 8 lenses with
+    """Query positions near caustics for the surrogate path: 64 lenses with
     log10 s ~ U[-0.5, 0.5], log10 q ~ U[-5, -1], log10 rho ~ U[-4, -2]; for
-    each, 24 positions = a random point of a random branch of the oracle's
+    each, 16 positions = a random point of a random branch of the oracle's
     caustic + a displacement uniform in a disc of 3x that branch's size."""
     rng = np.random.default_rng(404)
     rows = []
     jobs = []
-    for k in range(8):
+    for k in range(64):
         s = 10 ** rng.uniform(-0.5, 0.5)
         q = 10 ** rng.uniform(-5, -1)
         rho = 10 ** rng.uniform(-4, -2)
         _, cc = O.caustic(s, q, 256)
         pts = []
-        for _ in range(24):
+        for _ in range(16):
             b = rng.integers(4)
             c = cc[rng.integers(256), b]
             w = max(np.ptp(cc[:, b].real), np.ptp(cc[:, b].imag))
@@ -164,7 +216,7 @@ def surrogate_queries():
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
         for r in ex.map(run, jobs):
             rows.extend(r)
-    hdr = ("Surrogate queries: 8 lenses (seed 404) x 24 positions near the oracle's caustic (random branch point +\n"
+    hdr = ("Surrogate queries: 64 lenses (seed 404) x 16 positions near the oracle's caustic (random branch point +\n"
            "displacement within 3x the branch size); oracle magnifications.")
     _write("surrogate_queries.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
 
@@ -181,8 +233,9 @@ def central_wide():
            zip(range(y1.size), y1, y2, mu, st, nx))
 
 
-ALL = {"lightcurve_central": lightcurve_central, "central_wide": central_wide, "surrogate_queries": surrogate_queries, "map_planetary": map_planetary, "stress_resonant": stress_resonant,
-       "batch_lightcurves": batch_lightcurves, "paper_worked": paper_worked}
+ALL = {"lightcurve_central": lightcurve_central, "central_wide": central_wide, "surrogate_queries": surrogate_queries,
+       "map_planetary": map_planetary, "stress_resonant": stress_resonant, "batch_lightcurves": batch_lightcurves,
+       "paper_worked": paper_worked, "stress_resonant_1e4": stress_resonant_1e4}
 
 if __name__ == "__main__":
     names = sys.argv[1:] or list(ALL)

@@ -54,3 +54,21 @@ def test_central_wide_rows():
     assert np.array_equal(y1[idx], [float(r[1]) for r in rows])
     mu, st, nx = O.mag(c["s"], c["q"], c["rho"], y1[idx], y2[idx], scan_K=256)
     assert np.allclose(mu, [float(r[3]) for r in rows], rtol=RTOL, atol=0)
+
+
+# (file, status column, crossing-count column, crossing rows required)
+FILES = [("lightcurve_central.txt", 2, 3, 64), ("map_planetary.txt", 4, 5, 64), ("batch_lightcurves.txt", 4, 5, 64),
+         ("stress_resonant.txt", 4, 5, 0), ("stress_resonant_1e4.txt", 4, 5, 0), ("surrogate_queries.txt", 6, 7, 0),
+         ("central_wide.txt", 4, 5, 0), ("paper_worked.txt", 7, 8, 0)]
+
+
+@pytest.mark.parametrize("name,scol,xcol,nx", FILES)
+def test_every_golden_row_converged_and_crossings_covered(name, scol, xcol, nx):
+    """No stored value carries an oracle status other than 0 (every quadrature
+    reached its target and the two crossing detectors agreed), and the map and
+    the light-curve sets include at least 64 positions whose limb crosses the
+    caustic."""
+    rows = load(name)
+    assert rows
+    assert all(int(r[scol]) == 0 for r in rows), [r for r in rows if int(r[scol]) != 0][:3]
+    assert sum(int(r[xcol]) >= 2 for r in rows) >= nx
