@@ -452,10 +452,10 @@ static __device__ __noinline__ int limb_sample(const LensK &L, double th, cxd z[
     cxd c[6];
     eq6_coeffs(L.s, L.m2, y, c);
     if (!roots_finite(z)) initial_roots(L.s, y, z);
-    float dpa[5];
-    int f = solve_quintic<PREC, RP>(c, z, dpa, 60, wc.sw64, wc.sw32, wc.nw64);
+    float dpa[5], ca[6];
+    int f = solve_quintic<PREC, RP>(c, z, dpa, 60, wc.sw64, wc.sw32, wc.nw64, ca);
     SampleRefs o = {&ar.theta[slot], &ar.roots[slot * 5], &ar.zp[slot * 5], &ar.w[slot * 5], &ar.meta[slot]};
-    f |= classify_store(L, y, dzeta, c, z, dpa, th, o);
+    f |= classify_store(L, y, dzeta, ca, z, dpa, th, o);
     return f;
 }
 

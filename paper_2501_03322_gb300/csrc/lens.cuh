@@ -88,6 +88,14 @@ __device__ __forceinline__ void abs_coeffs(const cxd c[6], float ca[6]) {
 #pragma unroll
     for (int k = 0; k < 6; k++) ca[k] = sqrtf(norm2f(c[k]));
 }
+// The same, keeping the FP32 values of the coefficients.
+__device__ __forceinline__ void abs_coeffs(const cxd c[6], float ca[6], cxf cf[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        cf[k] = to_f(c[k]);
+        ca[k] = sqrtf(norm2(cf[k]));
+    }
+}
 
 // Horner round-off bound sum_k |c_k| |z|^k (the attainable residual |p(z)|).
 __device__ __forceinline__ float horner_bound(const float ca[6], float az) {
@@ -140,11 +148,9 @@ __device__ __forceinline__ cxf widen(cxf s, cxf) { return s; }
 // when the magnitudes may have changed.
 // RP = true keeps the pair loop rolled too (a smaller kernel; faster where
 // the warps of a CTA work on different lenses, slower on a single lens).
+// Pair sums S_i = sum_{j != i} 1/(z_i - z_j) and K2_i = sum_{j != i} 1/|z_i - z_j|^2.
 template <typename T, bool RP = false>
-__device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6], cx<T> z[5], float dpa[5],
-                                             float rtol, float eps, float thr[5], float az2[5], bool &fresh) {
-    cxf S[5];
-    float K2[5];
+__device__ __forceinline__ void pair_sums(const cx<T> z[5], cxf S[5], float K2[5]) {
 #pragma unroll
     for (int i = 0; i < 5; i++) { S[i] = {0.f, 0.f}; K2[i] = 0.f; }
     constexpr int PU = RP ? 1 : 5;
@@ -159,6 +165,22 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
             K2[i] += rr;
             K2[j] += rr;
         }
+}
+
+// PRE = true: S and K2 are given (pair sums of the current z, formed by the
+// caller) and, with fresh, so are the |z_i|^2 in az2.
+template <typename T, bool RP = false, bool PRE = false>
+__device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6], cx<T> z[5], float dpa[5],
+                                             float rtol, float eps, float thr[5], float az2[5], bool &fresh,
+                                             const cxf *Sp = nullptr, const float *K2p = nullptr) {
+    cxf S[5];
+    float K2[5];
+    if (PRE) {
+#pragma unroll
+        for (int i = 0; i < 5; i++) { S[i] = Sp[i]; K2[i] = K2p[i]; }
+    } else {
+        pair_sums<T, RP>(z, S, K2);
+    }
     cx<T> w[5];
     float wa2[5], wmax = 0.f;
     // not unrolled: one copy of the per-root code keeps the kernel's hot code
@@ -170,7 +192,7 @@ __device__ __forceinline__ bool aberth_sweep(const cx<T> c[6], const float ca[6]
         horner(c, z[i], p, d);
         w[i] = cdiv40(p, cmad(cx<T>{-p.x, -p.y}, widen(S[i], p), d));  // p / (p' - p S)
         if (fresh) {
-            az2[i] = norm2f(z[i]);
+            if (!PRE) az2[i] = norm2f(z[i]);
             const float az = sqrtf(az2[i]);
             const float dabs = sqrtf(norm2f(d));
             dpa[i] = dabs;
@@ -224,21 +246,23 @@ __device__ __forceinline__ bool roots_finite(const cxd z[5]) {
 // Roots of the quintic c starting from z (see the header comment).  sw64 and
 // sw32 count FP64 and FP32 Aberth sweeps (nw64, FP64 Newton passes, is kept
 // for the work counters and stays zero).  Returns SF_SOLVER when the iteration limit was reached.
+// ca receives |c_k| (FP32), which the classification reuses.
 template <int PREC, bool RP = false>
 __device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa[5], int maxit, int &sw64, int &sw32,
-                                             int &nw64) {
-    float ca[6];
-    abs_coeffs(c, ca);
+                                             int &nw64, float ca[6]) {
     if (PREC == 1) {
-        // scale to unit largest coefficient so FP32 neither under- nor overflows
-        const float cm = fmaxf(fmaxf(fmaxf(ca[0], ca[1]), fmaxf(ca[2], ca[3])), fmaxf(ca[4], ca[5]));
-        const double sc = 1.0 / (double)cm;
         cxf cf[6];
+        abs_coeffs(c, ca, cf);
+        // scale to unit largest coefficient so FP32 neither under- nor
+        // overflows in the iteration (in FP32: the FP32 copies of the
+        // coefficients are all the iteration uses)
+        const float cm = fmaxf(fmaxf(fmaxf(ca[0], ca[1]), fmaxf(ca[2], ca[3])), fmaxf(ca[4], ca[5]));
+        const float sc = 1.0f / cm;
         float caf[6];
 #pragma unroll
         for (int k = 0; k < 6; k++) {
-            cf[k] = to_f(sc * c[k]);
-            caf[k] = ca[k] / cm;
+            cf[k] = sc * cf[k];
+            caf[k] = ca[k] * sc;
         }
         cxf zf[5];
 #pragma unroll
@@ -254,10 +278,35 @@ __device__ __forceinline__ int solve_quintic(const cxd c[6], cxd z[5], float dpa
         }
         // FP64 Aberth sweeps from the FP32 roots: from FP32 accuracy the
         // cubic convergence estimate usually accepts the first sweep, which
-        // polishes all five roots at once
+        // polishes all five roots at once.  Where the pair loop is unrolled
+        // (!RP), the first sweep's pair sums are formed from the FP32 roots in
+        // FP32: z = to_d(zf) exactly, so zf_i - zf_j is the FP32-rounded exact
+        // difference, the same value the FP64 difference rounded to FP32
+        // gives, without FP64-pipe subtractions and conversions; likewise
+        // |z_i|^2.  (With the rolled pair loop of the 4-CTA instance this
+        // measured slower: the first sweep was then accepted only half as
+        // often, so that instance forms the sums in the sweep itself.)
+        cxf S[5];
+        float K2[5], thr[5], az2[5];
 #pragma unroll
         for (int i = 0; i < 5; i++) z[i] = to_d(zf[i]);
+        bool fresh = true;
+        int it0 = 0;
+        if (!RP) {
+            pair_sums<float, RP>(zf, S, K2);
+#pragma unroll
+            for (int i = 0; i < 5; i++) az2[i] = norm2(zf[i]);
+            sw64++;
+            it0 = 1;
+            if (aberth_sweep<double, RP, true>(c, ca, z, dpa, 1e-14f, 1.1e-16f, thr, az2, fresh, S, K2)) return 0;
+        }
+        for (int it = it0; it < maxit; it++) {
+            sw64++;
+            if (aberth_sweep<double, RP>(c, ca, z, dpa, 1e-14f, 1.1e-16f, thr, az2, fresh)) return 0;
+        }
+        return SF_SOLVER;
     }
+    abs_coeffs(c, ca);
     float thr[5], az2[5];
     bool fresh = true;
     for (int it = 0; it < maxit; it++) {
@@ -285,14 +334,12 @@ __device__ __forceinline__ int meta_index(uint32_t m, int k) { return (int)((m >
 // Classify the roots z of the sample at limb point y (secondary frame), with
 // limb tangent dzeta = i rho e^{i theta}; compute derivatives; store.
 // Returns the sample's status bits.
-__device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, const cxd c[6], const cxd z[5],
+__device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, const float ca[6], const cxd z[5],
                                               const float dpa[5], double theta, SampleRefs out) {
     cxd R[5];
     float aR[5], noise[5], Jf[5];
     bool Jpos[5];
     cxf f1f[5], d1f[5], d2f[5];
-    float ca[6];
-    abs_coeffs(c, ca);
     const float m1f = (float)L.m1, m2f = (float)L.m2;
     // the per-root loops here are not unrolled either (instruction cache)
 #pragma unroll 1

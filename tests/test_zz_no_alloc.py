@@ -53,61 +53,42 @@ def test_noalloc_matches_tw_mag_on_two_calls(prec):
 
 
 @pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
-def test_noalloc_central_caustic_against_oracle(prec):
-    """The central-caustic set (limbs crossing a tiny caustic next to its cusps,
-    magnifications up to 1e4): tw_mag_noalloc matches tw_mag_ex at the same
-    sample cap everywhere, and the oracle wherever that cap was not reached."""
+def test_noalloc_caustic_crossings_against_oracle(prec):
+    """Limbs that cross caustics, within the 512-sample cap of this entry
+    point: the central-caustic light curve (its 1000 positions, from the
+    oracle's trajectory) and the map cells within rho of the planetary caustic.
+    tw_mag_noalloc matches tw_mag_ex at the same cap everywhere, and the
+    oracle's stored values wherever that cap was not reached."""
     import os
 
-    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "central_wide.txt")
-    rows = [ln.split() for ln in open(gold) if not ln.startswith("#") and ln.strip()]
-    y1 = np.array([float(r[1]) for r in rows])
-    y2 = np.array([float(r[2]) for r in rows])
-    ref = np.array([float(r[3]) for r in rows])
-    ok = np.array([int(r[4]) == 0 for r in rows])
-    c = W.CENTRAL_WIDE
-    y1d = torch.as_tensor(y1, device="cuda")
-    y2d = torch.as_tensor(y2, device="cuda")
-    mu, err, ns, st = P.mag(c["s"], c["q"], c["rho"], y1d, y2d, rel_tol=c["rel_tol"], precision=prec,
-                            max_samples=512, details=True)
-    st = st.cpu().numpy()
-    mu = mu.cpu().numpy()
-    outd = torch.full_like(y1d, float("nan"))
-    assert P.lib().tw_mag_noalloc(c["s"], c["q"], c["rho"], ctypes.c_void_p(y1d.data_ptr()),
-                                  ctypes.c_void_p(y2d.data_ptr()), y1d.numel(), c["rel_tol"],
-                                  ctypes.c_void_p(outd.data_ptr()), prec, 512,
-                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == P.TW_OK
-    torch.cuda.synchronize()
-    got = outd.cpu().numpy()
-    assert np.max(np.abs(got / mu - 1.0)) <= TOL
-    clean = ok & ((st & P.POS_CAP) == 0)
-    assert clean.sum() >= 0.99 * len(rows)
-    assert np.max(np.abs(got[clean] / ref[clean] - 1.0)) <= TOL
+    import oracle as O
 
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
-@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
-def test_noalloc_runs_the_slope_repair_pass(prec):
-    """Positions whose caustic crossing fails the slope test (Sec. 2.4.2) within
-    512 limb samples, found among 2^20 seeded queries near caustics: tw_mag_ex
-    repairs them in its second pass, and tw_mag_noalloc, which has that pass
-    too, gives the same results (without it they differ by up to ~1e-3)."""
-    s, q, rho, y1, y2 = P.surrogate_sample(3, 1 << 20)
-    mu, err, ns, st = P.mag_multi(s, q, rho, y1, y2, rel_tol=TOL, precision=prec, max_samples=512, details=True)
-    torch.cuda.synchronize()
-    hit = np.nonzero((st.cpu().numpy() & P.POS_SLOPE) != 0)[0][:8]
-    assert hit.size >= 1
-    repaired = 0
-    for i in hit:
-        lens = [float(t[i]) for t in (s, q, rho)]
-        ref, _, _, st1 = P.mag(*lens, y1[i:i + 1], y2[i:i + 1], rel_tol=TOL, precision=prec, max_samples=512,
-                               details=True)
-        repaired += int(int(st1[0]) & P.POS_SLOPE != 0)
-        outd = torch.full_like(y1[i:i + 1], float("nan"))
-        for _ in range(2):
-            assert call_noalloc(*lens, y1[i:i + 1].contiguous(), y2[i:i + 1].contiguous(), outd, prec) == P.TW_OK
-            torch.cuda.synchronize()
-            assert abs(float(outd[0]) / float(ref[0]) - 1.0) <= 1e-12
-    assert repaired >= 1  # the repair pass ran on at least one of them
+    def rows(name):
+        return [ln.split() for ln in open(os.path.join(gold, name)) if not ln.startswith("#") and ln.strip()]
+
+    c = W.LIGHTCURVE_CENTRAL
+    lc = rows("lightcurve_central.txt")
+    y1, y2 = O.trajectory(c["u0"], c["alpha"], c["t0"], c["tE"], np.array([float(r[0]) for r in lc]))
+    cases = [((c["s"], c["q"], c["rho"]), y1, y2, np.array([float(r[1]) for r in lc]))]
+    m = W.MAP_PLANETARY
+    mp = [r for r in rows("map_planetary.txt") if int(r[5]) >= 2]
+    cases.append(((m["s"], m["q"], m["rho"]), np.array([float(r[1]) for r in mp]), np.array([float(r[2]) for r in mp]),
+                  np.array([float(r[3]) for r in mp])))
+    for lens, a, b, ref in cases:
+        y1d = torch.as_tensor(a, device="cuda")
+        y2d = torch.as_tensor(b, device="cuda")
+        mu, err, ns, st = P.mag(*lens, y1d, y2d, rel_tol=TOL, precision=prec, max_samples=512, details=True)
+        mu, st = mu.cpu().numpy(), st.cpu().numpy()
+        outd = torch.full_like(y1d, float("nan"))
+        assert call_noalloc(*lens, y1d, y2d, outd, prec) == P.TW_OK
+        torch.cuda.synchronize()
+        got = outd.cpu().numpy()
+        assert np.max(np.abs(got / mu - 1.0)) <= TOL
+        clean = (st & P.POS_CAP) == 0
+        assert clean.sum() >= 0.95 * len(ref)
+        assert np.max(np.abs(got[clean] / ref[clean] - 1.0)) <= TOL
 
 
 def test_noalloc_rejects_oversized_and_host_requests():
