@@ -398,6 +398,8 @@ def main():
     ap.add_argument("--graph", action="store_true", help="replay each launch from a CUDA graph")
     ap.add_argument("--gate", action="store_true",
                     help="single-lens workloads: point-source adequacy gate (tw_mag_gated) before contour integration")
+    ap.add_argument("--split", action="store_true",
+                    help="single-lens workloads: split the one workload across the ranks (strong scaling)")
     ap.add_argument("--limit", type=int, default=0,
                     help="use a seeded sub-sample of this many positions (small profiling captures)")
     args = ap.parse_args()
@@ -418,6 +420,11 @@ def main():
     cfg = config_of(wl, args.mode, args.gpus)
     cfg["autotune"] = bool(args.autotune)
     cfg["graph"] = bool(args.graph)
+    if args.split:
+        if wl["kind"] != "mag" or args.gate:
+            raise SystemExit("--split applies to the single-lens position workloads without --gate")
+        cfg["split"] = "contiguous ranges balanced by the previous step's limb samples, all-gathered"
+        cfg["parallelism"] = "split%d" % args.gpus
     if args.gate:
         if wl["kind"] != "mag":
             raise SystemExit("--gate applies to the single-lens position workloads")
@@ -460,6 +467,30 @@ def main():
         def step():
             _, nc = P.mag_gated(sd, qd_, rd, y1d, y2d, rel_tol=wl["rel_tol"], precision=prec, out=outd)
             wl["ncontour"].append(nc)
+    elif wl["kind"] == "mag" and args.split:
+        # one workload split across the ranks (strong scaling): contiguous
+        # ranges balanced by the limb samples of the previous step, results
+        # all-gathered (paper_2501_03322_gb300.shard)
+        from paper_2501_03322_gb300 import shard
+
+        y1d, y2d = D(wl["y1"]), D(wl["y2"])
+        wl["costs"] = None
+
+        def step():
+            def compute(lo, hi):
+                mu, _, ns, _ = P.mag(wl["s"], wl["q"], wl["rho"], y1d[lo:hi], y2d[lo:hi], rel_tol=wl["rel_tol"],
+                                     details=True, **kw)
+                wl["ns"] = ns.to(torch.float64)
+                return mu
+
+            if dist is None:
+                out, bounds = compute(0, wl["n"]), np.array([0, wl["n"]])
+                wl["costs"] = wl["ns"].cpu().numpy()
+            else:
+                out, bounds = shard.run_sharded(wl["n"], compute, dist, costs=wl["costs"], device=dev)
+                wl["costs"] = shard.gather(wl["ns"], bounds, dist, dev).cpu().numpy()
+            wl["out"] = out
+            wl["bounds"] = bounds
     elif wl["kind"] == "mag":
         y1d, y2d = D(wl["y1"]), D(wl["y2"])
         outd = torch.empty_like(y1d)
@@ -536,7 +567,7 @@ def main():
     t_step = max_over_ranks(t_step, dist, dev)
     if dist:
         dist.barrier()
-    value = world * wl["n"] / t_step
+    value = (1 if args.split else world) * wl["n"] / t_step
     extra = {}
     if wl.get("gate"):
         extra = {"gate": {"contour_fraction": sum(wl["ncontour"][-args.steps:]) / (args.steps * wl["n"])}}
@@ -580,6 +611,17 @@ def main():
 
         def e2e_step():
             P.mag_gated(*[t.numpy() for t in hin], rel_tol=wl["rel_tol"], precision=prec, out=hout.numpy())
+    elif wl["kind"] == "mag" and args.split:
+        # this rank's range of the last step, from pinned host buffers
+        lo, hi = int(wl["bounds"][rank]), int(wl["bounds"][rank + 1])
+        hy1 = torch.from_numpy(np.ascontiguousarray(wl["y1"][lo:hi])).pin_memory()
+        hy2 = torch.from_numpy(np.ascontiguousarray(wl["y2"][lo:hi])).pin_memory()
+        hout = torch.empty(hi - lo, dtype=torch.float64).pin_memory()
+        h2d, d2h = 16 * (hi - lo), 9 * (hi - lo)
+
+        def e2e_step():
+            P.mag(wl["s"], wl["q"], wl["rho"], hy1.numpy(), hy2.numpy(), rel_tol=wl["rel_tol"], precision=prec,
+                  out=hout.numpy())
     elif wl["kind"] == "mag":
         hy1 = torch.from_numpy(np.ascontiguousarray(wl["y1"])).pin_memory()
         hy2 = torch.from_numpy(np.ascontiguousarray(wl["y2"])).pin_memory()
@@ -666,10 +708,11 @@ def main():
                       "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"})
 
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f32+f64", "data": "synthetic",
+            "scaling": "strong" if args.split else "weak",
             "config": cfg, "roofline": roof, "clocks": clocks,
-            "e2e": {"value": world * wl["n"] / t_e2e, "unit": unit, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": (1 if args.split else world) * wl["n"] / t_e2e, "unit": unit, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches(wl, args.steps),
             "roofline_other": other,

@@ -31,7 +31,10 @@
  * never frees or retains caller memory.
  *
  * Errors: a negative return code means nothing was written (argument errors
- * are detected before any device work).  TW_OK means every output element was
+ * are detected before any device work).  The environment variable
+ * TW_DEVICE_MEMORY_LIMIT (bytes; unset or 0 = none) caps the device working
+ * memory the library allocates for contour integration: a call that would
+ * need more returns TW_ENOMEM and writes nothing.  TW_OK means every output element was
  * written; per-position outcomes are reported in opts->pos_status when given.
  * A positive return (warning) is only produced by synchronous (host-pointer)
  * calls, after all outputs were written.
@@ -286,6 +289,14 @@ int tw_peak_probe(int kind, double *flops_per_s);
  * one-step reciprocal used for the Aberth correction (about 40 bits).
  * Synchronous.  The paper has no counterpart. */
 int tw_selftest(double *rcp_max_rel_err);
+
+/* Device self-test of the library's bounded waits (no counterpart in the
+ * paper; a failure-detection hook): one CTA waits on an mbarrier that nothing
+ * arrives on, with poll_limit polls (1..2^24), through the wait routine of
+ * the tensor-core GEMM, and gives up.  Returns TW_ETIMEOUT when the wait gave
+ * up and reported it (the expected outcome), TW_OK if it did not.
+ * Synchronous on the legacy default stream; the context stays usable. */
+int tw_selftest_timeout(unsigned int poll_limit);
 
 /* Device self-test of the slope test and its repair (Sec. 2.4.2) on a planted
  * misjudgment.  The limb of the source (s, q <= 1, rho, centre y1, y2) is

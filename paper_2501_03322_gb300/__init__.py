@@ -93,6 +93,8 @@ def lib():
             L.tw_last_launch_ms.restype = I
             L.tw_selftest_slope.argtypes = [d, d, d, d, d, P, I, I, P]
             L.tw_selftest_slope.restype = I
+            L.tw_selftest_timeout.argtypes = [ctypes.c_uint]
+            L.tw_selftest_timeout.restype = I
             L.tw_peak_probe.argtypes = [I, P]
             L.tw_peak_probe.restype = I
             L.tw_selftest.argtypes = [P]

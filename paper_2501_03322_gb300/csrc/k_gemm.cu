@@ -11,7 +11,8 @@
 // commits them to the stage's mbarrier, and the four warps read the 128 x 128
 // FP32 accumulator back from tensor memory (warp w owns rows 32w..32w+31).
 // Every mbarrier wait is bounded; on a timeout the kernel records an error
-// flag, waits (bounded) for its own MMAs, frees its tensor memory and exits.
+// flag, waits once more (bounded) for its own MMAs, frees its tensor memory
+// and exits.
 #include <cuda_bf16.h>
 
 #include "../../include/twinkle.h"
@@ -84,6 +85,14 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn_kernel(GemmArgs g) {
     // wait for the last commit (it covers every earlier MMA)
     bool ok = true;
     if (issued > 0) ok = mbar_wait(&bar[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1), GEMM_WAIT_LIMIT);
+    if (!__syncthreads_and(ok) && issued > 0) {
+        // the MMAs are still not complete: wait once more, four times as
+        // long, before the tensor memory they write is released below (a
+        // CTA must free its tensor memory, or later CTAs on this SM could not
+        // allocate any); the error flag makes the host discard C either way
+        ok = false;
+        (void)mbar_wait(&bar[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1), 4u * GEMM_WAIT_LIMIT);
+    }
     ok = __syncthreads_and(ok) && !failed;
     if (ok) {
         tc_fence_after();
@@ -161,6 +170,41 @@ extern "C" int tw_gemm_bf16(const void *A, const void *B, int M, int N, int K, f
     if (e == cudaSuccess) e = gemm_bf16_tn(g, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(err);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return TW_ECUDA; }
+    return h ? TW_ETIMEOUT : TW_OK;
+}
+
+// ------------------------------------------------------------------ self-test
+// A bounded wait that must run out: one CTA waits on an mbarrier that nothing
+// arrives on (no copy or MMA is in flight), with `limit` polls, through the
+// same wait routine the GEMM uses; on giving up it records the error flag and
+// returns, leaving the context usable.
+namespace tw {
+__global__ void timeout_selftest_kernel(uint32_t limit, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0u, limit);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicExch(err, 1);
+}
+}  // namespace tw
+
+extern "C" int tw_selftest_timeout(unsigned int poll_limit) {
+    using namespace tw;
+    if (poll_limit == 0 || poll_limit > (1u << 24)) return TW_EINVAL;
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) { (void)cudaGetLastError(); return TW_ENOMEM; }
+    int h = 0;
+    cudaError_t e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        timeout_selftest_kernel<<<1, 32>>>(poll_limit, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(err);
     if (e != cudaSuccess) { (void)cudaGetLastError(); return TW_ECUDA; }
     return h ? TW_ETIMEOUT : TW_OK;

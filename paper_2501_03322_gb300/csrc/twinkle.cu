@@ -88,8 +88,21 @@ static int dev_state(DevState **out) {
     return TW_OK;
 }
 
+// Optional cap on the library's device working memory, in bytes
+// ($TW_DEVICE_MEMORY_LIMIT; unset or 0: no cap): a request beyond it fails
+// with TW_ENOMEM as a failed cudaMalloc would, before anything is freed or
+// allocated.  It lets callers bound the library's footprint and lets tests
+// make an allocation fail without exhausting a GPU.
+static size_t memory_limit() {
+    const char *v = getenv("TW_DEVICE_MEMORY_LIMIT");
+    if (!v || !*v) return 0;
+    return (size_t)strtoull(v, nullptr, 10);
+}
+
 static int grow(char **buf, size_t *have, size_t need) {
     if (*have >= need) return TW_OK;
+    const size_t lim = memory_limit();
+    if (lim && need > lim) return TW_ENOMEM;
     if (*buf) {
         cudaDeviceSynchronize();
         cudaFree(*buf);
@@ -341,6 +354,10 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     if (opts_in) o = *opts_in;
     if (check_opts(&o)) return TW_EINVAL;
     if (c.n == 0) return TW_OK;
+    // the smallest sample arena any launch needs (one CTA) must fit the cap:
+    // checked before any device work, so nothing is written
+    const size_t lim = memory_limit();
+    if (lim && arena_slot_bytes((o.max_samples + 63) & ~63) * WPB > lim) return TW_ENOMEM;
     std::lock_guard<std::mutex> lk(g_mu);
     DevState *dp = nullptr;
     int rc = dev_state(&dp);

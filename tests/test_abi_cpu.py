@@ -97,3 +97,17 @@ def test_no_gpu_reports_cuda_error_not_a_fallback():
     assert _mag(n=4) == P.TW_ECUDA
     with pytest.raises(P.TwError):
         P.mag(1.0, 1e-3, 1e-3, np.zeros(3), np.zeros(3))
+
+
+def test_device_memory_cap_refuses_before_device_work(monkeypatch):
+    """With TW_DEVICE_MEMORY_LIMIT below the smallest sample arena a launch
+    needs, the call returns TW_ENOMEM before any device work and writes
+    nothing (allocation failure injected on the host, no GPU involved)."""
+    monkeypatch.setenv("TW_DEVICE_MEMORY_LIMIT", "4096")
+    y = np.array([0.1, 0.2, 0.3, 0.4])
+    out = np.full(4, -7.0)
+    rc = P.lib().tw_mag_ex(1.0, 1e-3, 1e-3, y.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p), 4,
+                           1e-4, out.ctypes.data_as(ctypes.c_void_p), None)
+    assert rc == P.TW_ENOMEM
+    assert (out == -7.0).all()
+    assert "memory" in P.status_str(rc)
