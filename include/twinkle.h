@@ -106,9 +106,19 @@ typedef struct tw_opts {
     double *err_out;      /* optional [n]: error estimate of mu (absolute) */
     int32_t *nsamp_out;   /* optional [n]: limb samples used */
     int8_t *pos_status;   /* optional [n]: TW_POS_* bits */
+    int warps_per_position; /* 1 (default): one warp integrates each position;
+                             2 or 4: that many warps of a CTA integrate each
+                             position together, one new limb sample per lane
+                             per iteration (32 x warps per iteration;
+                             samples_per_iter is then ignored) -- fewer
+                             positions in flight, each finished sooner, for
+                             workloads too small to fill the GPU (the paper
+                             uses a block of threads per source, Sec. 3).
+                             With autotune = 1 the autotuner chooses it. */
 } tw_opts;
 
-/* Fills *opts with the defaults listed above (all output pointers NULL). */
+/* Fills *opts with the defaults listed above (all output pointers NULL).
+ * tw_opts grows only at its end; fill it with tw_opts_default first. */
 void tw_opts_default(tw_opts *opts);
 
 /* Finite-source magnification of n source positions (y1[i], y2[i]) behind

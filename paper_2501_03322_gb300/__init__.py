@@ -50,6 +50,7 @@ class TwOpts(ctypes.Structure):
         ("err_out", ctypes.c_void_p),
         ("nsamp_out", ctypes.c_void_p),
         ("pos_status", ctypes.c_void_p),
+        ("warps_per_position", ctypes.c_int),
     ]
 
 
@@ -152,9 +153,10 @@ def _alloc_like(ref, n, dtype_np, dtype_torch_name):
 
 
 def make_opts(precision=PREC_FP64, samples_per_iter=64, max_samples=4096, stream=None, err=None, nsamp=None,
-              status=None, autotune=False, use_graph=False) -> TwOpts:
+              status=None, autotune=False, use_graph=False, warps_per_position=1) -> TwOpts:
     o = TwOpts()
     lib().tw_opts_default(ctypes.byref(o))
+    o.warps_per_position = int(warps_per_position)
     o.autotune = int(bool(autotune))
     o.use_graph = int(bool(use_graph))
     o.precision = int(precision)
@@ -281,7 +283,7 @@ def selftest_rcp() -> tuple:
 
 
 def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64, max_samples=4096,
-        out=None, details=False, stream=None, autotune=False, use_graph=False):
+        out=None, details=False, stream=None, autotune=False, use_graph=False, warps_per_position=1):
     """Finite-source magnification of positions (y1[i], y2[i]) (tw_mag_ex).
 
     Returns ``out`` or, with details=True, (out, err, nsamp, status)."""
@@ -295,7 +297,7 @@ def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=6
         nsamp = _alloc_like(y1, n, np.int32, "int32")
         status = _alloc_like(y1, n, np.int8, "int8")
     o = make_opts(precision, samples_per_iter, max_samples, _stream_of(y1, stream), err, nsamp, status, autotune,
-                  use_graph)
+                  use_graph, warps_per_position)
     _check(lib().tw_mag_ex(s, q, rho, _ptr(y1), _ptr(y2), n, rel_tol, _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
 
@@ -317,7 +319,7 @@ def mag_noalloc(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, max_sample
 
 
 def mag_multi(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64, max_samples=4096,
-              out=None, details=False, stream=None, autotune=False, use_graph=False):
+              out=None, details=False, stream=None, autotune=False, use_graph=False, warps_per_position=1):
     """Magnification of positions each with its own lens and source radius (tw_mag_multi)."""
     arrs = [_prep(a) for a in (s, q, rho, y1, y2)]
     n = int(arrs[0].shape[0])
@@ -329,7 +331,7 @@ def mag_multi(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_
         nsamp = _alloc_like(arrs[0], n, np.int32, "int32")
         status = _alloc_like(arrs[0], n, np.int8, "int8")
     o = make_opts(precision, samples_per_iter, max_samples, _stream_of(arrs[0], stream), err, nsamp, status,
-                  autotune, use_graph)
+                  autotune, use_graph, warps_per_position)
     _check(lib().tw_mag_multi(*[_ptr(a) for a in arrs], n, rel_tol, _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
 
@@ -350,7 +352,7 @@ def mag_gated(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, max_samples=
 
 
 def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,
-               max_samples=4096, out=None, details=False, stream=None, autotune=False, use_graph=False):
+               max_samples=4096, out=None, details=False, stream=None, autotune=False, use_graph=False, warps_per_position=1):
     """Magnification along a straight-line trajectory (tw_lightcurve_ex)."""
     times = _prep(times)
     n = int(times.shape[0])
@@ -362,13 +364,13 @@ def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC
         nsamp = _alloc_like(times, n, np.int32, "int32")
         status = _alloc_like(times, n, np.int8, "int8")
     o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status, autotune,
-                  use_graph)
+                  use_graph, warps_per_position)
     _check(lib().tw_lightcurve_ex(s, q, rho, u0, alpha, t0, tE, _ptr(times), n, rel_tol, _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
 
 
 def lightcurve_batch(params, offsets, times, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=64,
-                     max_samples=4096, out=None, details=False, stream=None, autotune=False, use_graph=False):
+                     max_samples=4096, out=None, details=False, stream=None, autotune=False, use_graph=False, warps_per_position=1):
     """Many light curves in one launch (tw_lightcurve_batch).
 
     params: [ncurve, 7] (s, q, rho, u0, alpha, t0, tE); offsets: [ncurve + 1] int64."""
@@ -389,7 +391,7 @@ def lightcurve_batch(params, offsets, times, rel_tol=1e-4, precision=PREC_FP64, 
         nsamp = _alloc_like(times, total, np.int32, "int32")
         status = _alloc_like(times, total, np.int8, "int8")
     o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status, autotune,
-                  use_graph)
+                  use_graph, warps_per_position)
     _check(lib().tw_lightcurve_batch(_ptr(params), _ptr(offsets), _ptr(times), ncurve, rel_tol, _ptr(out),
                                      ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out

@@ -487,14 +487,48 @@ static __device__ __noinline__ int slope_repairs(const Arena &ar, const uint16_t
     return __shfl_sync(FULL, f, 0);
 }
 
+constexpr int CTA_WARPS = 4;  // warps per CTA of the contour kernels
+
+// Cooperation of the W warps (1, 2 or 4 of a CTA's four) that integrate one
+// position together: a barrier over the group, and one exchange slot per warp
+// in shared memory for the group's sums, scans and compactions.  Every
+// decision that ends a loop is taken from values read back from these slots
+// after a barrier, so all warps of a group take it alike.
+struct Exch {
+    double a, e, scan, last_th;
+    unsigned long long first;
+    int cnt, last_pos, flags, pad;
+};
+
+template <int W>
+struct Coop {
+    Exch *ex;  // this group's W slots
+    int wig;   // warp index in the group
+    int bar;   // named barrier of the group (W = 2: 1 or 2, 64 threads each)
+    __device__ __forceinline__ void sync() const {
+        if (W == 1) __syncwarp();
+        else if (W == CTA_WARPS) __syncthreads();
+        else if (bar == 1) asm volatile("bar.sync 1, 64;" ::: "memory");
+        else asm volatile("bar.sync 2, 64;" ::: "memory");
+    }
+};
+
 // REPAIR = false: a crossing that fails the slope test only sets PS_SLOPE
 // (the position is then integrated again by the REPAIR = true instance, which
 // repairs such crossings as they appear).  Keeping the repair code out of the
 // main instance keeps its register allocation unchanged.
-template <int PREC, int SPL, bool REPAIR, bool RP = false>
-__device__ PosResult integrate_position(const LensK &L, double tol, int cap, const Arena &ar, WarpStage &ws) {
-    constexpr int SPI = 32 * SPL;
+// W warps share the position: 32 W SPL samples per iteration, lane gl = 32 wig
+// + lane of the group taking samples gl SPL .. gl SPL + SPL - 1 of a batch.
+// PosResult.work is this warp's own share.
+template <int PREC, int SPL, bool REPAIR, bool RP = false, int W = 1>
+__device__ PosResult integrate_position(const LensK &L, double tol, int cap, const Arena &ar, WarpStage &ws,
+                                        const Coop<W> &co) {
+    static_assert(!REPAIR || W == 1, "the repair pass runs one warp per position");
+    static_assert(W == 1 || W == 2 || W == CTA_WARPS, "1, 2 or 4 warps per position");
+    static_assert(32 * SPL * W <= 256, "a batch must fit the shared-memory stage");
+    constexpr int SPI = 32 * SPL * W;
     const int lane = threadIdx.x & 31;
+    const int gl = co.wig * 32 + lane;
     const double twopi = 6.283185307179586476925287;
     const double minsep = 1e-15 / L.rho + 1e-14;
     int flags = 0;
@@ -507,7 +541,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
     // source centres exactly on a lens are a common input.  This solve only
     // provides starting points (every sample is then iterated to full FP64
     // accuracy in either mode), so it runs in FP32 from a cold start; it is
-    // the same on every lane of the warp.
+    // the same on every lane (and every warp of a group).
     const cxd yw = {L.y0.x + 0.5 * L.rho * 0.7648421872844885, L.y0.y + 0.5 * L.rho * 0.6442176872376911};
     cxd zc[5];
     unsigned cmask = 0x1fu;  // real images of the warm-start point
@@ -584,7 +618,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
     const float wx = (float)(yw.x - L.y0.x), wy = (float)(yw.y - L.y0.y), rhof = (float)L.rho;
 #pragma unroll
     for (int t = 0; t < SPL; t++) {
-        const int k = lane * SPL + t;
+        const int k = gl * SPL + t;
         const double th = twopi * k / SPI;
         cxd z[5] = {zc[0], zc[1], zc[2], zc[3], zc[4]};
         float sn, cs;
@@ -597,14 +631,14 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
         flags |= limb_sample<PREC, RP>(L, th, z, ar, k, wc);
         ar.ordA[k] = (uint16_t)k;
     }
-    __syncwarp();
+    co.sync();
 #pragma unroll
     for (int t = 0; t < SPL; t++) {
-        const int k = lane * SPL + t;
+        const int k = gl * SPL + t;
         if (compute_edge(ar, k, (k + 1 == SPI) ? 0 : k + 1, twopi / SPI, &ar.eA[k], &ar.eE[k])) vpos = k;
         wc.edges++;
     }
-    __syncwarp();
+    co.sync();
 
     int N = SPI, nslot = SPI;
     uint16_t *ordA = ar.ordA, *ordB = ar.ordB;
@@ -618,20 +652,28 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
         }
         vpos = -1;
         double a = 0.0, e = 0.0;
-        for (int p = lane; p < N; p += 32) {
+        for (int p = gl; p < N; p += 32 * W) {
             const int sl = ordA[p];
             a += ar.eA[sl];
             e += ar.eE[sl];
         }
         A = warp_sum(a);
         E = warp_sum(e);
+        if (W > 1) {
+            if (lane == 0) { co.ex[co.wig].a = A; co.ex[co.wig].e = E; }
+            co.sync();
+            A = 0.0;
+            E = 0.0;
+#pragma unroll
+            for (int w = 0; w < W; w++) { A += co.ex[w].a; E += co.ex[w].e; }
+        }
         if (!(E > tol * fabs(A))) break;          // converged (or non-finite)
         if (nslot + SPI > cap) { flags |= PS_CAP; break; }
 
         // cumulative error in theta order, each edge less its share of the tolerance
         const double thr = tol * fabs(A) * rcp((double)N);
-        const int chunk = (N + 31) >> 5;
-        const int p0 = min(lane * chunk, N), p1 = min(p0 + chunk, N);
+        const int chunk = (N + 32 * W - 1) / (32 * W);
+        const int p0 = min(gl * chunk, N), p1 = min(p0 + chunk, N);
         double run = 0.0;
         for (int p = p0; p < p1; p++) {
             run += fmax(ar.eE[ordA[p]] - thr, 0.0);
@@ -643,10 +685,24 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
             const double v = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += v;
         }
-        const double W = __shfl_sync(FULL, incl, 31);
-        const double excl = incl - run;
+        double Wsum = __shfl_sync(FULL, incl, 31);
+        double excl = incl - run;
+        if (W > 1) {
+            // warp totals in group order: offsets of the later warps
+            if (lane == 31) co.ex[co.wig].scan = incl;
+            co.sync();
+            double off = 0.0, tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                const double v = co.ex[w].scan;
+                if (w < co.wig) off += v;
+                tot += v;
+            }
+            excl += off;
+            Wsum = tot;
+        }
         for (int p = p0; p < p1; p++) ar.cum[p] += excl;
-        __syncwarp();
+        co.sync();
 
         // inverse transform at quantiles (j + 1/2)/SPI with linear interpolation
         double tn[SPL];
@@ -654,8 +710,8 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
         bool tk[SPL];
 #pragma unroll
         for (int t = 0; t < SPL; t++) {
-            const int j = lane * SPL + t;
-            const double target = (j + 0.5) * (W / SPI);
+            const int j = gl * SPL + t;
+            const double target = (j + 0.5) * (Wsum / SPI);
             int lo = 0, hi = N - 1;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
@@ -671,13 +727,22 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
             tp[t] = lo;
             tk[t] = (tn[t] - ta > minsep) && (tb - tn[t] > minsep);
         }
-        // drop a quantile that coincides with the previous one
+        // drop a quantile that coincides with the previous one (the previous
+        // warp's last quantile for the first lane of a warp of a group)
+        double pth_w = 0.0;
+        int ppos_w = -1;
+        if (W > 1) {
+            if (lane == 31) { co.ex[co.wig].last_th = tn[SPL - 1]; co.ex[co.wig].last_pos = tp[SPL - 1]; }
+            co.sync();
+            if (co.wig > 0) { pth_w = co.ex[co.wig - 1].last_th; ppos_w = co.ex[co.wig - 1].last_pos; }
+        }
 #pragma unroll
         for (int t = 0; t < SPL; t++) {
             double pth = __shfl_up_sync(FULL, tn[SPL - 1], 1);
             int ppos = __shfl_up_sync(FULL, tp[SPL - 1], 1);
             if (t > 0) { pth = tn[t - 1]; ppos = tp[t - 1]; }
-            const bool has_prev = (t > 0) || (lane > 0);
+            else if (W > 1 && lane == 0) { pth = pth_w; ppos = ppos_w; }
+            const bool has_prev = (t > 0) || (gl > 0);
             if (has_prev && ppos == tp[t] && fabs(tn[t] - pth) <= minsep) tk[t] = false;
         }
         // compaction of the kept angles, in quantile order
@@ -688,6 +753,19 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
             const unsigned b = __ballot_sync(FULL, tk[t]);
             before += __popc(b & lt);
             m += __popc(b);
+        }
+        if (W > 1) {
+            if (lane == 0) co.ex[co.wig].cnt = m;
+            co.sync();
+            int off = 0, tot = 0;
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                const int c = co.ex[w].cnt;
+                if (w < co.wig) off += c;
+                tot += c;
+            }
+            before += off;
+            m = tot;
         }
         int rk[SPL];
         {
@@ -705,7 +783,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
                 ws.theta_new[rk[t]] = tn[t];
                 ws.pos_new[rk[t]] = (uint16_t)tp[t];
             }
-        __syncwarp();
+        co.sync();
 
         // new samples, warm-started from the sample at the start of their interval
 #pragma unroll
@@ -735,7 +813,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
 #pragma unroll
         for (int t = 0; t < SPL; t++)
             if (tk[t]) ordB[tp[t] + 1 + rk[t]] = (uint16_t)(nslot + rk[t]);
-        __syncwarp();
+        co.sync();
         uint16_t *tmp = ordA; ordA = ordB; ordB = tmp;
         const int nslot_old = nslot;
         N += m;
@@ -759,10 +837,18 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
                     wc.edges++;
                 }
             }
-        __syncwarp();
+        co.sync();
 
     }
     flags = __reduce_or_sync(FULL, flags);
+    if (W > 1) {
+        if (lane == 0) co.ex[co.wig].flags = flags;
+        co.sync();
+        flags = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) flags |= co.ex[w].flags;
+        co.sync();
+    }
     PosResult r;
     r.work.sw64 = __reduce_add_sync(FULL, wc.sw64);
     r.work.sw32 = __reduce_add_sync(FULL, wc.sw32);

@@ -1,0 +1,7 @@
+// Kernel instance: FP64 root iterations, 2 warps integrate each position, one new limb
+// sample per lane per iteration (64 per iteration).
+#include "kernels.cuh"
+
+namespace tw {
+TW_DEFINE_LAUNCHER_W(0, 2)
+}

@@ -111,11 +111,22 @@ __device__ __forceinline__ bool fetch_position(const WorkSrc &w, int64_t idx, Po
 // REPAIR = false: the main pass over src.n work items.  REPAIR = true: the
 // repair pass over the work items that the main pass queued in kp.relist
 // (crossings that failed the slope test), integrated again with repairs.
-template <int PREC, int SPL, bool REPAIR, int OCC = TW_MIN_CTAS_PER_SM>
+// W = 1, 2 or 4 warps integrate each position together (the group's first
+// warp takes the work items and writes the outputs; the group uses one arena
+// slot and one shared-memory stage).
+template <int PREC, int SPL, bool REPAIR, int OCC = TW_MIN_CTAS_PER_SM, int W = 1>
 __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
+    static_assert(WPB == CTA_WARPS, "CTA shape");
     __shared__ WarpStage stage[WPB];
+    __shared__ Exch exch[WPB];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * WPB + wib;
+    const int grp = wib / W;
+    Coop<W> co;
+    co.ex = &exch[grp * W];
+    co.wig = wib % W;
+    co.bar = 1 + grp;
+    const int gw = blockIdx.x * (WPB / W) + grp;  // the group's arena slot
+    const bool leader = co.wig == 0 && lane == 0;
     const Arena ar = arena_at(kp.arena, kp.slot_bytes, kp.cap, gw);
     unsigned long long n = (unsigned long long)kp.src.n;
     if (REPAIR) n = min(*(volatile unsigned long long *)(kp.counter + 6), kp.relist_cap);
@@ -123,8 +134,16 @@ __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
     for (;;) {
         if (it >= end) {
             unsigned long long first = 0;
-            if (lane == 0) first = atomicAdd(kp.counter + (REPAIR ? 7 : 0), (unsigned long long)kp.chunk);
-            it = __shfl_sync(FULL, first, 0);
+            if (leader) first = atomicAdd(kp.counter + (REPAIR ? 7 : 0), (unsigned long long)kp.chunk);
+            if (W > 1) {
+                if (leader) co.ex[0].first = first;
+                co.sync();
+                first = co.ex[0].first;
+                co.sync();
+            } else {
+                first = __shfl_sync(FULL, first, 0);
+            }
+            it = first;
             end = it + (unsigned long long)kp.chunk;
             if (end > n) end = n;
             if (it >= end) break;
@@ -149,10 +168,11 @@ __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
             L.y0 = {y1 - P.s * L.m1, P.y2};  // centre-of-mass -> secondary frame
             // the 4-CTA instance serves per-position lenses: its root solver
             // keeps the pair loop rolled as well (see aberth_sweep)
-            const PosResult r = integrate_position<PREC, SPL, REPAIR, (OCC >= 4)>(L, kp.tol, kp.cap, ar, stage[wib]);
+            const PosResult r =
+                integrate_position<PREC, SPL, REPAIR, (OCC >= 4), W>(L, kp.tol, kp.cap, ar, stage[grp * W], co);
             // a crossing failed the slope test: queue the position for the
             // repair pass (its outputs below are overwritten there)
-            if (!REPAIR && (r.status & PS_SLOPE) && kp.relist && lane == 0) {
+            if (!REPAIR && (r.status & PS_SLOPE) && kp.relist && leader) {
                 const unsigned long long k = atomicAdd(kp.counter + 6, 1ull);
                 if (k < kp.relist_cap) kp.relist[k] = (int64_t)idx;
             }
@@ -161,8 +181,8 @@ __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
             err = r.err * inv_src;
             nsamp = r.nsamp;
             status = r.status;
-            if (lane == 0) {
-                atomicAdd(kp.counter + 1, (unsigned long long)r.nsamp);
+            if (lane == 0) {  // every warp adds its own work; the sample count once
+                if (co.wig == 0) atomicAdd(kp.counter + 1, (unsigned long long)r.nsamp);
                 atomicAdd(kp.counter + 2, (unsigned long long)r.work.sw64);
                 atomicAdd(kp.counter + 3, (unsigned long long)r.work.sw32);
                 atomicAdd(kp.counter + 4, (unsigned long long)r.work.edges);
@@ -170,7 +190,7 @@ __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
             }
             if (!isfinite(mu)) { status |= PS_NONFINITE; mu = __longlong_as_double(0x7ff8000000000000ll); }
         }
-        if (lane == 0) {
+        if (leader) {
             const unsigned long long o = (kp.src.kind == 3 && kp.src.list) ? (unsigned long long)kp.src.list[idx] : idx;
             kp.out[o] = mu;
             if (kp.err) kp.err[o] = err;
@@ -203,6 +223,17 @@ __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
     }                                                                                              \
     cudaError_t occupancy_contour_##PREC##_##SPL##_o##OCC(int *occ) {                              \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, contour_kernel<PREC, SPL, false, OCC>, TPB, 0); \
+    }
+
+// An instance in which W warps integrate each position (one sample per lane).
+#define TW_DEFINE_LAUNCHER_W(PREC, W)                                                              \
+    cudaError_t launch_contour_##PREC##_w##W(unsigned blocks, cudaStream_t st, const KParams &kp) { \
+        contour_kernel<PREC, 1, false, TW_MIN_CTAS_PER_SM, W><<<blocks, TPB, 0, st>>>(kp);          \
+        return cudaGetLastError();                                                                  \
+    }                                                                                               \
+    cudaError_t occupancy_contour_##PREC##_w##W(int *occ) {                                         \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, contour_kernel<PREC, 1, false, TW_MIN_CTAS_PER_SM, W>, \
+                                                             TPB, 0);                               \
     }
 
 // The repair-pass instance of a precision (two samples per lane).
@@ -238,6 +269,14 @@ cudaError_t launch_contour_0_2_o4(unsigned blocks, cudaStream_t st, const KParam
 cudaError_t occupancy_contour_0_2_o4(int *occ);
 cudaError_t launch_contour_1_2_o4(unsigned blocks, cudaStream_t st, const KParams &kp);
 cudaError_t occupancy_contour_1_2_o4(int *occ);
+cudaError_t launch_contour_0_w2(unsigned blocks, cudaStream_t st, const KParams &kp);
+cudaError_t occupancy_contour_0_w2(int *occ);
+cudaError_t launch_contour_1_w2(unsigned blocks, cudaStream_t st, const KParams &kp);
+cudaError_t occupancy_contour_1_w2(int *occ);
+cudaError_t launch_contour_0_w4(unsigned blocks, cudaStream_t st, const KParams &kp);
+cudaError_t occupancy_contour_0_w4(int *occ);
+cudaError_t launch_contour_1_w4(unsigned blocks, cudaStream_t st, const KParams &kp);
+cudaError_t occupancy_contour_1_w4(int *occ);
 cudaError_t launch_repair_0(unsigned blocks, cudaStream_t st, const KParams &kp);
 cudaError_t launch_repair_1(unsigned blocks, cudaStream_t st, const KParams &kp);
 

@@ -23,7 +23,17 @@ namespace tw {
 typedef cudaError_t (*launch_fn)(unsigned, cudaStream_t, const KParams &);
 typedef cudaError_t (*occ_fn)(int *);
 
-static void pick_kernel(int prec, int spl, bool occ4, launch_fn *lf, occ_fn *of) {
+static void pick_kernel(int prec, int spl, bool occ4, int w, launch_fn *lf, occ_fn *of) {
+    if (w == 2) {
+        if (prec == 0) { *lf = launch_contour_0_w2; *of = occupancy_contour_0_w2; }
+        else { *lf = launch_contour_1_w2; *of = occupancy_contour_1_w2; }
+        return;
+    }
+    if (w == 4) {
+        if (prec == 0) { *lf = launch_contour_0_w4; *of = occupancy_contour_0_w4; }
+        else { *lf = launch_contour_1_w4; *of = occupancy_contour_1_w4; }
+        return;
+    }
     if (spl == 2 && occ4) {
         if (prec == 0) { *lf = launch_contour_0_2_o4; *of = occupancy_contour_0_2_o4; }
         else { *lf = launch_contour_1_2_o4; *of = occupancy_contour_1_2_o4; }
@@ -124,17 +134,20 @@ static int check_opts(const tw_opts *o) {
     const int spi = o->samples_per_iter;
     if (spi != 32 && spi != 64 && spi != 128) return TW_EINVAL;
     if (o->max_samples < 64 || o->max_samples > 16384 || o->max_samples < spi) return TW_EINVAL;
+    const int w = o->warps_per_position;
+    if (w != 0 && w != 1 && w != 2 && w != 4) return TW_EINVAL;
+    if (o->max_samples < 32 * (w > 1 ? w : 1)) return TW_EINVAL;
     return TW_OK;
 }
 
-// Launch shape: samples per lane per iteration (limb samples per iteration =
-// 32 x spl), CTAs per SM (0: as many as fit), work items per atomic grab, and
-// which compiled instance: occ4 = 1 the one built for 4 CTAs per SM (spl 2
-// only), 0 the one built for 2, -1 by work kind (4 for per-position lenses,
-// whose warps diverge most; measured 5% faster there and 8% slower on a
-// single-lens map).
+// Launch shape: samples per lane per iteration, CTAs per SM (0: as many as
+// fit), work items per atomic grab, which compiled instance (occ4 = 1 the one
+// built for 4 CTAs per SM (spl 2 only), 0 the one built for 2, -1 by work
+// kind: see launch()), and w, the warps that integrate each position together
+// (1; or 2 or 4 with one sample per lane).  Limb samples per iteration =
+// 32 x spl x w.
 struct LaunchCfg {
-    int spl, ctas, chunk, occ4;
+    int spl, ctas, chunk, occ4, w;
 };
 
 // Launches the contour kernel over src.n positions.  Device pointers only.
@@ -147,15 +160,25 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     if (src.stride < 1) src.stride = 1;
     launch_fn lf;
     occ_fn of;
-    const bool occ4 = cfg.occ4 > 0 || (cfg.occ4 < 0 && src.kind == 3);
-    pick_kernel(prec, cfg.spl, occ4, &lf, &of);
+    int w = (cfg.w == 2 || cfg.w == 4) ? cfg.w : 1;
+    // per-position lenses, untuned, at 64 samples per iteration: two warps
+    // per position (measured on 2^18 queries near caustics, mixed precision:
+    // 136 ms, against 149 ms for the 4-CTA instance and 177 ms for one warp
+    // per position)
+    if (w == 1 && cfg.occ4 < 0 && src.kind == 3 && cfg.spl == 2) {
+        w = 2;
+        cfg.spl = 1;
+    }
+    const bool occ4 = w == 1 && (cfg.occ4 > 0 || (cfg.occ4 < 0 && src.kind == 3));
+    pick_kernel(prec, cfg.spl, occ4, w, &lf, &of);
     int occ = 0;
     cudaError_t e = of(&occ);
     if (e != cudaSuccess) return cuda_fail(e);
     if (occ < 1) occ = 1;
     if (cfg.ctas > 0 && cfg.ctas < occ) occ = cfg.ctas;
     int64_t blocks = (int64_t)d.nsm * occ;
-    const int64_t need_blocks = (src.n + WPB - 1) / WPB;
+    const int per_cta = WPB / w;  // positions in flight per CTA
+    const int64_t need_blocks = (src.n + per_cta - 1) / per_cta;
     if (blocks > need_blocks) blocks = need_blocks;
     if (blocks < 1) blocks = 1;
     const size_t slot_bytes = arena_slot_bytes(cap);
@@ -259,8 +282,10 @@ static void tune_load() {
         if (!bar) continue;
         LaunchCfg c;
         c.occ4 = -1;
-        if (sscanf(bar + 1, "%d %d %d %d", &c.spl, &c.ctas, &c.chunk, &c.occ4) < 3) continue;
+        c.w = 1;
+        if (sscanf(bar + 1, "%d %d %d %d %d", &c.spl, &c.ctas, &c.chunk, &c.occ4, &c.w) < 3) continue;
         if (c.spl != 1 && c.spl != 2 && c.spl != 4) continue;
+        if (c.w != 1 && c.w != 2 && c.w != 4) continue;
         *bar = 0;
         g_tune[line] = c;
     }
@@ -274,8 +299,8 @@ static void tune_save() {
     FILE *f = fopen(path.c_str(), "w");
     if (!f) return;
     for (auto &kv : g_tune)
-        fprintf(f, "%s|%d %d %d %d\n", kv.first.c_str(), kv.second.spl, kv.second.ctas, kv.second.chunk,
-                kv.second.occ4);
+        fprintf(f, "%s|%d %d %d %d %d\n", kv.first.c_str(), kv.second.spl, kv.second.ctas, kv.second.chunk,
+                kv.second.occ4, kv.second.w);
     fclose(f);
 }
 
@@ -292,9 +317,10 @@ static int autotune(DevState &d, const WorkSrc &src, double tol, int prec, int m
     auto it = g_tune.find(key);
     if (it != g_tune.end()) { *best = it->second; return TW_OK; }
     // the sub-sample must give every resident warp a dozen positions or more,
-    // otherwise the timing measures the tail of the launch, not its throughput
+    // otherwise the timing measures the tail of the launch, not its
+    // throughput; a workload smaller than that is timed whole (it is then
+    // tail-bound, which is what warps per position address)
     const int64_t warps = (int64_t)d.nsm * 2 * WPB;
-    if (src.n < 8 * warps) return TW_OK;  // too small to time reliably: keep the defaults
     int64_t ncal = src.n / 20;
     if (ncal < 16 * warps) ncal = 16 * warps;
     if (ncal > 65536) ncal = 65536;
@@ -308,14 +334,15 @@ static int autotune(DevState &d, const WorkSrc &src, double tol, int prec, int m
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
     float best_ms = 3.0e38f;
-    // (samples per lane, compiled instance): the 4-CTA instance exists for 2
-    const int spls[4] = {1, 2, 4, 2}, occs[4] = {0, 0, 0, 1};
+    // (samples per lane, compiled instance, warps per position): the 4-CTA
+    // instance exists for 2 samples per lane, the cooperative ones for 1
+    const int spls[6] = {1, 2, 4, 2, 1, 1}, occs[6] = {0, 0, 0, 1, 0, 0}, ws[6] = {1, 1, 1, 1, 2, 4};
     const int ctass[2] = {1, 0};
     const int chunks[2] = {1, 4};
-    for (int a = 0; a < 4; a++)
+    for (int a = 0; a < 6; a++)
         for (int b = 0; b < 2; b++)
             for (int c = 0; c < 2; c++) {
-                const LaunchCfg cfg = {spls[a], ctass[b], chunks[c], occs[a]};
+                const LaunchCfg cfg = {spls[a], ctass[b], chunks[c], occs[a], ws[a]};
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; rep++) {  // first run warms the arena and caches
                     cudaEventRecord(e0, st);
@@ -375,7 +402,11 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     if (o.nsamp_out && ptr_kind(o.nsamp_out) != kind) return TW_EINVAL;
     if (o.pos_status && ptr_kind(o.pos_status) != kind) return TW_EINVAL;
     const void *din[5];
-    LaunchCfg cfg = {o.samples_per_iter / 32, 0, 1, -1};
+    LaunchCfg cfg = {o.samples_per_iter / 32, 0, 1, -1, 1};
+    if (o.warps_per_position == 2 || o.warps_per_position == 4) {
+        cfg.w = o.warps_per_position;
+        cfg.spl = 1;
+    }
     if (dev) {
         for (int i = 0; i < c.nin; i++) din[i] = c.in[i];
         WorkSrc src = bind(din);
@@ -443,7 +474,7 @@ int contour_positions(const double *s, const double *q, const double *rho, const
     w.y1 = y1;
     w.y2 = y2;
     w.list = list;
-    const LaunchCfg cfg = {2, 0, 1, -1};
+    const LaunchCfg cfg = {2, 0, 1, -1, 1};
     return launch(*dp, w, tol, prec, max_samples, cfg, false, out, nullptr, nullptr, status, st);
 }
 
@@ -460,6 +491,7 @@ void tw_opts_default(tw_opts *o) {
     o->samples_per_iter = 64;
     o->max_samples = 4096;
     o->autotune = 0;
+    o->warps_per_position = 1;
 }
 
 int tw_mag_ex(double s, double q, double rho, const double *y1, const double *y2, int64_t n, double rel_tol,

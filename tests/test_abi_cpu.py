@@ -56,7 +56,7 @@ def test_invalid_arguments_rejected(kw):
 
 def test_invalid_options_rejected():
     for field, val in [("precision", 7), ("samples_per_iter", 48), ("samples_per_iter", 256), ("max_samples", 16),
-                       ("max_samples", 1 << 20)]:
+                       ("max_samples", 1 << 20), ("warps_per_position", 3), ("warps_per_position", 8)]:
         o = P.TwOpts()
         P.lib().tw_opts_default(ctypes.byref(o))
         setattr(o, field, val)

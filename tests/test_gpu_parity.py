@@ -348,3 +348,46 @@ def test_point_source_gate_device_arrays_regrow(prec):
     assert 0 < nc < n2
     assert rel_err(mu[:len(idx)][mok], mref[mok]).max() <= TOL
     assert rel_err(mu[len(idx):][sok], sref[sok]).max() <= TOL
+
+
+@pytest.mark.parametrize("w", [2, 4])
+@pytest.mark.parametrize("prec", MODES)
+def test_warps_per_position(prec, w):
+    """2 or 4 warps integrating each position together (a block of threads per
+    source, Sec. 3): the central-caustic light curve, all 1000 points, and the
+    map's caustic-crossing cells, against the oracle."""
+    c = W.LIGHTCURVE_CENTRAL
+    rows = load("lightcurve_central.txt")
+    t = np.array([float(r[0]) for r in rows])
+    ref = np.array([float(r[1]) for r in rows])
+    mu, err, ns, st = P.lightcurve(c["s"], c["q"], c["rho"], c["u0"], c["alpha"], c["t0"], c["tE"], dev(t),
+                                   rel_tol=c["rel_tol"], precision=prec, details=True, warps_per_position=w)
+    torch.cuda.synchronize()
+    assert rel_err(mu.cpu().numpy(), ref).max() <= TOL
+    assert (st.cpu().numpy() & (P.POS_IMAGECOUNT | P.POS_NONFINITE)).sum() == 0
+    assert (ns.cpu().numpy() % (32 * w) == 0).all()  # whole batches of 32 w samples
+    m = W.MAP_PLANETARY
+    mr = [r for r in load("map_planetary.txt") if int(r[5]) >= 2]
+    y1 = np.array([float(r[1]) for r in mr])
+    y2 = np.array([float(r[2]) for r in mr])
+    mu = P.mag(m["s"], m["q"], m["rho"], dev(y1), dev(y2), rel_tol=m["rel_tol"], precision=prec,
+               warps_per_position=w)
+    assert rel_err(mu.cpu().numpy(), np.array([float(r[3]) for r in mr])).max() <= TOL
+
+
+def test_autotuned_small_workload_chooses_warps(tmp_path, monkeypatch):
+    """A workload too small to fill the GPU (the 1000-point light curve) is
+    timed whole by the autotuner, whose choice includes the warps per
+    position; the tuned result stays within the tolerance of the oracle."""
+    monkeypatch.setenv("TW_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    c = W.LIGHTCURVE_CENTRAL
+    rows = load("lightcurve_central.txt")
+    t = np.array([float(r[0]) for r in rows])
+    ref = np.array([float(r[1]) for r in rows])
+    mu = P.lightcurve(c["s"], c["q"], c["rho"], c["u0"], c["alpha"], c["t0"], c["tE"], dev(t), rel_tol=c["rel_tol"],
+                      precision=P.PREC_MIXED, autotune=True)
+    torch.cuda.synchronize()
+    assert rel_err(mu.cpu().numpy(), ref).max() <= TOL
+    # the cache file holds every shape tuned in this process; take the light curve's (work kind 1)
+    line = [ln for ln in open(tmp_path / "tune.txt") if "prec=1;tol=1e-4;kind=1|" in ln][0].split("|")[1].split()
+    assert len(line) == 5 and int(line[4]) in (1, 2, 4)
