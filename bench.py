@@ -114,6 +114,14 @@ def workload(name):
         params, offsets, times = W.batch_lightcurves()
         return dict(kind="batch", name="batch_lightcurves_4096", params=params, offsets=offsets, times=times,
                     rel_tol=W.BATCH_LIGHTCURVES["rel_tol"], n=times.size)
+    if name in W.FIG4:
+        c = W.FIG4[name]
+        y1, y2 = W.fig4_grid(name)
+        return dict(kind="mag", name=name + "_480x340", s=c["s"], q=c["q"], rho=c["rho"], y1=y1, y2=y2, rel_tol=1e-4,
+                    n=y1.size, golden="fig4_maps.txt", golden_map=name)
+    if name == "fig6_sweep":
+        a = W.fig6_sweep()
+        return dict(kind="multi", name="fig6_sweep_64x900", arrays=a, rel_tol=1e-4, n=a[0].size)
     raise SystemExit("unknown workload " + name)
 
 
@@ -238,6 +246,21 @@ def golden_errors(wl, prec, P, wpath=None):
         got, _ = P.surrogate_mag(wpath, *[a[ok, k].copy() for k in range(5)], rel_tol=wl["rel_tol"],
                                  kappa=wl["kappa"], precision=prec)
         ref, name = a[ok, 5], "surrogate_queries.txt"
+    elif wl["kind"] == "multi":
+        name = "fig6_sweep.txt"
+        a = np.array([[float(v) for v in r[1:8]] for r in golden_rows(name)])
+        a = a[a[:, 6] == 0]
+        got, err_est, _, _ = P.mag_multi(*[a[:, k].copy() for k in range(5)], rel_tol=wl["rel_tol"], precision=prec,
+                                         details=True)
+        ref = a[:, 5]
+    elif wl["kind"] == "mag" and wl.get("golden_map"):
+        name = wl["golden"]
+        rows = [r for r in golden_rows(name) if r[0] == wl["golden_map"] and int(r[5]) == 0]
+        y1 = np.array([float(r[2]) for r in rows])
+        y2 = np.array([float(r[3]) for r in rows])
+        ref = np.array([float(r[4]) for r in rows])
+        got, err_est, _, _ = P.mag(wl["s"], wl["q"], wl["rho"], y1, y2, rel_tol=wl["rel_tol"], precision=prec,
+                                   details=True)
     elif wl["kind"] == "mag":
         name = "stress_resonant_1e4.txt" if wl["name"].startswith("stress") else "map_planetary.txt"
         rows = [r for r in golden_rows(name) if int(r[4]) == 0]
@@ -292,6 +315,12 @@ def cpu_oracle_sample(wl, k, seed=777, cores=None):
             list(ex.map(lambda r: O.mag(r[0], r[1], r[2], [r[3]], [r[4]], nthreads=1), a))
         return len(a), time.perf_counter() - t0, cores
     idx = W.sample_indices(int(wl["n"]), k, seed=seed)
+    if wl["kind"] == "multi":  # per-position lens: spread the positions over the cores
+        a = np.array([x[idx] for x in wl["arrays"]]).T
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(lambda r: O.mag(r[0], r[1], r[2], [r[3]], [r[4]], nthreads=1), a))
+        return len(a), time.perf_counter() - t0, cores
     t0 = time.perf_counter()
     if wl["kind"] == "mag":
         O.mag(wl["s"], wl["q"], wl["rho"], wl["y1"][idx], wl["y2"][idx], nthreads=cores)
@@ -387,7 +416,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="surrogate",
                     choices=["map_planetary", "lightcurve_central", "stress_resonant", "batch_lightcurves",
-                             "surrogate"])
+                             "surrogate", "fig4_s05", "fig4_s1", "fig4_s3", "fig6_sweep"])
     ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-sample", type=int, default=64, help="positions in the CPU oracle baseline sample")
     ap.add_argument("--ref-sample", type=int, default=24, help="positions per step of the reference arm")
@@ -497,6 +526,12 @@ def main():
 
         def step():
             P.mag(wl["s"], wl["q"], wl["rho"], y1d, y2d, rel_tol=wl["rel_tol"], out=outd, **kw)
+    elif wl["kind"] == "multi":
+        md = [D(a) for a in wl["arrays"]]
+        outd = torch.empty_like(md[0])
+
+        def step():
+            P.mag_multi(*md, rel_tol=wl["rel_tol"], out=outd, **kw)
     elif wl["kind"] == "lc":
         td = D(wl["times"])
         outd = torch.empty_like(td)
@@ -631,6 +666,14 @@ def main():
         def e2e_step():
             P.mag(wl["s"], wl["q"], wl["rho"], hy1.numpy(), hy2.numpy(), rel_tol=wl["rel_tol"], precision=prec,
                   autotune=args.autotune, out=hout.numpy())
+    elif wl["kind"] == "multi":
+        hm = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in wl["arrays"]]
+        hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()
+        h2d, d2h = 40 * wl["n"], 8 * wl["n"]
+
+        def e2e_step():
+            P.mag_multi(*[t.numpy() for t in hm], rel_tol=wl["rel_tol"], precision=prec, autotune=args.autotune,
+                        out=hout.numpy())
     elif wl["kind"] == "lc":
         ht = torch.from_numpy(np.ascontiguousarray(wl["times"])).pin_memory()
         hout = torch.empty(wl["n"], dtype=torch.float64).pin_memory()

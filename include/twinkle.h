@@ -146,6 +146,19 @@ int tw_lightcurve(double s, double q, double rho, double u0, double alpha, doubl
 int tw_lightcurve_ex(double s, double q, double rho, double u0, double alpha, double t0, double tE,
                      const double *times, int64_t n, double rel_tol, double *out, const tw_opts *opts);
 
+/* Light curve of an orbiting binary lens.  The paper names lens orbital
+ * motion as the case contour integration handles flexibly (Sec. 1), without
+ * a formula; this library takes the first-order (linear) reading: at time t
+ * the separation is s + ds_dt (t - t0) and the binary axis has turned so that
+ * the trajectory angle is alpha + dalpha_dt (t - t0), the trajectory being
+ * that of tw_lightcurve with these values (ds_dt in Einstein radii per unit
+ * of t, dalpha_dt in radians per unit of t).  A time whose separation is not
+ * positive gives NaN and TW_POS_NONFINITE.  With ds_dt = dalpha_dt = 0 the
+ * results equal tw_lightcurve_ex's. */
+int tw_lightcurve_orbital(double s, double q, double rho, double u0, double alpha, double t0, double tE,
+                          double ds_dt, double dalpha_dt, const double *times, int64_t n, double rel_tol, double *out,
+                          const tw_opts *opts);
+
 /* Many light curves of uneven length in one persistent, work-stealing launch.
  * params: [ncurve][7] float64 rows (s, q, rho, u0, alpha, t0, tE);
  * offsets: [ncurve + 1] int64, offsets[0] = 0, non-decreasing; curve k owns

@@ -17,6 +17,7 @@ source; in short:
 * ``close_approaches`` -- limb angles where the caustic nearly touches the limb
 * ``caustic``      -- critical curve J = 0 and its caustic image
 * ``trajectory``   -- straight-line source trajectory of a light curve
+* ``lightcurve_orbital`` -- light curve of a lens with linear orbital motion
 * ``rayshoot``     -- brute-force inverse ray shooting (Sec. 1), for pinning ``mag``
 
 Per-position status codes from ``mag``: 0 ok, 1 crossing detectors disagree or
@@ -206,6 +207,35 @@ def lightcurve(s, q, rho, u0, alpha, t0, tE, times, scan_K: int = 256, nthreads:
     """Magnification along a straight-line trajectory."""
     y1, y2 = trajectory(u0, alpha, t0, tE, times)
     return mag(s, q, rho, y1, y2, scan_K=scan_K, nthreads=nthreads)
+
+
+def lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, ds_dt, dalpha_dt, times, scan_K: int = 256, nthreads: int = 0):
+    """Magnification along a straight-line trajectory behind an orbiting lens
+    whose separation and axis angle change linearly in time: at time t the lens
+    has separation s + ds_dt (t - t0) and the trajectory angle is alpha +
+    dalpha_dt (t - t0) (the first-order reading of lens orbital motion).  Each
+    time is its own lens: one ``mag`` per time, spread over threads."""
+    import concurrent.futures as cf
+
+    t = np.ascontiguousarray(np.atleast_1d(times), dtype=np.float64)
+    st = s + ds_dt * (t - t0)
+    at = alpha + dalpha_dt * (t - t0)
+
+    def one(i):
+        y1, y2 = trajectory(u0, at[i], t0, tE, t[i:i + 1])
+        if not st[i] > 0:
+            return np.nan, ORC_INPUT_STATUS, 0
+        m, s_, n_ = mag(st[i], q, rho, y1, y2, scan_K=scan_K, nthreads=1)
+        return m[0], s_[0], n_[0]
+
+    workers = nthreads if nthreads > 0 else (os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        res = list(ex.map(one, range(t.size)))
+    return (np.array([r[0] for r in res]), np.array([r[1] for r in res], np.int32),
+            np.array([r[2] for r in res], np.int32))
+
+
+ORC_INPUT_STATUS = STATUS_INPUT
 
 
 def rayshoot(s, q, rho, y1, y2, box, npix: int, nthreads: int = 0) -> float:

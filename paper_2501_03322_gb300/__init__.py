@@ -78,6 +78,8 @@ def lib():
             L.tw_lightcurve.restype = I
             L.tw_lightcurve_ex.argtypes = [d, d, d, d, d, d, d, P, i64, d, P, P]
             L.tw_lightcurve_ex.restype = I
+            L.tw_lightcurve_orbital.argtypes = [d, d, d, d, d, d, d, d, d, P, i64, d, P, P]
+            L.tw_lightcurve_orbital.restype = I
             L.tw_mag_multi.argtypes = [P, P, P, P, P, i64, d, P, P]
             L.tw_mag_gated.argtypes = [P, P, P, P, P, i64, d, P, P, P]
             L.tw_mag_gated.restype = I
@@ -366,6 +368,25 @@ def lightcurve(s, q, rho, u0, alpha, t0, tE, times, rel_tol=1e-4, precision=PREC
     o = make_opts(precision, samples_per_iter, max_samples, _stream_of(times, stream), err, nsamp, status, autotune,
                   use_graph, warps_per_position)
     _check(lib().tw_lightcurve_ex(s, q, rho, u0, alpha, t0, tE, _ptr(times), n, rel_tol, _ptr(out), ctypes.byref(o)))
+    return (out, err, nsamp, status) if details else out
+
+
+def lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, ds_dt, dalpha_dt, times, rel_tol=1e-4, precision=PREC_FP64,
+                       max_samples=4096, out=None, details=False, stream=None, warps_per_position=1):
+    """Light curve of an orbiting lens, s and alpha linear in time (tw_lightcurve_orbital)."""
+    times = _prep(times)
+    n = int(times.shape[0])
+    if out is None:
+        out = _alloc_like(times, n, np.float64, "float64")
+    err = nsamp = status = None
+    if details:
+        err = _alloc_like(times, n, np.float64, "float64")
+        nsamp = _alloc_like(times, n, np.int32, "int32")
+        status = _alloc_like(times, n, np.int8, "int8")
+    o = make_opts(precision, 64, max_samples, _stream_of(times, stream), err, nsamp, status, False, False,
+                  warps_per_position)
+    _check(lib().tw_lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, ds_dt, dalpha_dt, _ptr(times), n, rel_tol,
+                                       _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
 
 

@@ -30,11 +30,13 @@ constexpr int WPB = TPB / 32;
 // Where the positions of a launch come from.
 struct WorkSrc {
     int kind;  // 0: one lens, arrays of positions; 1: one light curve; 2: batch of light curves;
-               // 3: per-position lens (surrogate fallback and training labels)
+               // 3: per-position lens (surrogate fallback and training labels);
+               // 4: one light curve of an orbiting lens (s and alpha linear in time)
     int64_t n;
     double s, q, rho;                      // kinds 0 and 1
     const double *y1, *y2;                 // kind 0
-    double u0, alpha, t0, tE;              // kind 1
+    double u0, alpha, t0, tE;              // kinds 1 and 4
+    double ds_dt, dalpha_dt;               // kind 4: rates of the separation and of the binary axis angle
     const double *times;                   // kinds 1 and 2
     const double *params;                  // kind 2: [ncurve][7]
     const int64_t *offsets;                // kind 2: [ncurve + 1]
@@ -86,6 +88,11 @@ __device__ __forceinline__ bool fetch_position(const WorkSrc &w, int64_t idx, Po
     } else if (w.kind == 1) {
         P.s = w.s; P.q = w.q; P.rho = w.rho;
         trajectory(w.u0, w.alpha, w.t0, w.tE, w.times[idx], P.y1, P.y2);
+    } else if (w.kind == 4) {
+        // the binary's separation and axis angle change linearly with time
+        const double dt = w.times[idx] - w.t0;
+        P.s = w.s + w.ds_dt * dt; P.q = w.q; P.rho = w.rho;
+        trajectory(w.u0, w.alpha + w.dalpha_dt * dt, w.t0, w.tE, w.times[idx], P.y1, P.y2);
     } else if (w.kind == 3) {
         const int64_t j = w.list ? (int64_t)w.list[idx] : idx;
         P.s = w.ps[j]; P.q = w.pq[j]; P.rho = w.prho[j];

@@ -538,6 +538,28 @@ int tw_lightcurve_ex(double s, double q, double rho, double u0, double alpha, do
     });
 }
 
+int tw_lightcurve_orbital(double s, double q, double rho, double u0, double alpha, double t0, double tE,
+                          double ds_dt, double dalpha_dt, const double *times, int64_t n, double rel_tol, double *out,
+                          const tw_opts *opts) {
+    if (n < 0 || !finite_pos(s) || !finite_pos(q) || !finite_pos(rho) || !finite_pos(rel_tol) || !finite_pos(tE) ||
+        !isfinite(u0) || !isfinite(alpha) || !isfinite(t0) || !isfinite(ds_dt) || !isfinite(dalpha_dt))
+        return TW_EINVAL;
+    if (n > 0 && (!times || !out)) return TW_EINVAL;
+    Call c;
+    c.nin = 1;
+    c.in[0] = times; c.insz[0] = (size_t)n * 8;
+    c.n = n;
+    return run_call(c, rel_tol, opts, out, [&](const void **din) {
+        WorkSrc w;
+        memset(&w, 0, sizeof(w));
+        w.kind = 4; w.n = n; w.s = s; w.q = q; w.rho = rho; w.stride = 1;
+        w.u0 = u0; w.alpha = alpha; w.t0 = t0; w.tE = tE;
+        w.ds_dt = ds_dt; w.dalpha_dt = dalpha_dt;
+        w.times = (const double *)din[0];
+        return w;
+    });
+}
+
 int tw_lightcurve(double s, double q, double rho, double u0, double alpha, double t0, double tE,
                   const double *times, int64_t n, double rel_tol, double *out) {
     return tw_lightcurve_ex(s, q, rho, u0, alpha, t0, tE, times, n, rel_tol, out, nullptr);

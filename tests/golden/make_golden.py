@@ -17,6 +17,12 @@ Files (text, one position per line: inputs, mu, oracle status):
   paper_worked.txt        the paper's worked configurations (Fig. 1, 2, 5)
   surrogate_queries.txt   1024 positions near the caustics of 64 lenses of the surrogate's range
   central_wide.txt        4096 centres on the central caustic of a wide planetary lens
+  lightcurve_orbital.txt  200 points of a central-caustic light curve of an orbiting lens (separation
+                          and axis angle linear in time)
+  fig4_maps.txt           the paper's three Fig. 4 grids (480 x 340, q = 1e-4): per map 128
+                          random cells and 64 cells within rho of the caustic
+  fig6_sweep.txt          the (s, q) sweep (64 pairs x 30 x 30, rho = 1e-4): 4 random positions
+                          of every pair
 
 Positions "near the caustic" are chosen with the oracle's caustic (nearest of
 its sampled points within rho of the limb's centre).
@@ -233,9 +239,66 @@ def central_wide():
            zip(range(y1.size), y1, y2, mu, st, nx))
 
 
+ORBITAL = dict(s=1.0, q=1e-3, rho=1e-3, u0=0.01, alpha=1.0, t0=0.0, tE=20.0, ds_dt=0.03, dalpha_dt=0.2)
+
+
+def lightcurve_orbital():
+    c = ORBITAL
+    t = np.linspace(-1.0, 1.0, 200)
+    mu, st, nx = O.lightcurve_orbital(c["s"], c["q"], c["rho"], c["u0"], c["alpha"], c["t0"], c["tE"], c["ds_dt"],
+                                      c["dalpha_dt"], t, scan_K=256)
+    hdr = ("Central-caustic light curve of an orbiting lens: s=1 + 0.03 (t - t0), q=1e-3, rho=1e-3, u0=0.01,\n"
+           "alpha=1 + 0.2 (t - t0) rad, t0=0, tE=20 d, 200 times linspace(-1, 1); oracle magnifications.")
+    _write("lightcurve_orbital.txt", hdr, ["t", "mu", "status", "ncross"], zip(t, mu, st, nx))
+
+
+def fig4_maps():
+    rows = []
+    for k, name in enumerate(sorted(W.FIG4)):
+        c = W.FIG4[name]
+        y1, y2 = W.fig4_grid(name)
+        idx = W.sample_indices(y1.size, 128, seed=600 + k)
+        near = np.nonzero(_near_caustic(np.c_[y1, y2], c["s"], c["q"], c["rho"]))[0]
+        near = np.setdiff1d(near, idx)
+        extra = np.sort(np.random.default_rng(610 + k).choice(near, size=min(64, near.size), replace=False))
+        idx = np.r_[idx, extra]
+        mu, st, nx = O.mag(c["s"], c["q"], c["rho"], y1[idx], y2[idx], scan_K=256)
+        rows += [(name, i, a, b, m, t, x) for i, a, b, m, t, x in zip(idx, y1[idx], y2[idx], mu, st, nx)]
+    path = os.path.join(HERE, "fig4_maps.txt")
+    with open(path, "w") as f:
+        f.write("# The paper's Fig. 4 speed maps (Sec. 4.1): q = 1e-4, s = 0.5 (rho 5e-5), 1 (rho 1e-3), 3 (rho 1e-4),\n")
+        f.write("# 480 x 340 cells (workloads.fig4_grid); per map 128 random cells (seeds 600..602) and 64 cells\n")
+        f.write("# within rho of the oracle's caustic (seeds 610..612); oracle magnifications.\n")
+        f.write("# columns: map index y1 y2 mu status ncross\n")
+        for r in rows:
+            f.write("%s %d %r %r %r %d %d\n" % (r[0], int(r[1]), float(r[2]), float(r[3]), float(r[4]), int(r[5]), int(r[6])))
+    print("wrote", path, len(rows), "rows")
+
+
+def fig6_sweep():
+    S, Q, R, Y1, Y2 = W.fig6_sweep()
+    g2 = W.FIG6_GRID ** 2
+    rng = np.random.default_rng(620)
+    idx = np.concatenate([k * g2 + np.sort(rng.choice(g2, 4, replace=False)) for k in range(len(W.FIG6_BOXES))])
+
+    def run(k):
+        sel = idx[4 * k:4 * k + 4]
+        mu, st, nx = O.mag(S[sel[0]], Q[sel[0]], R[sel[0]], Y1[sel], Y2[sel], scan_K=256, nthreads=1)
+        return [(i, S[i], Q[i], R[i], Y1[i], Y2[i], m, a, b) for i, m, a, b in zip(sel, mu, st, nx)]
+
+    rows = []
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
+        for r in ex.map(run, range(len(W.FIG6_BOXES))):
+            rows.extend(r)
+    hdr = ("The (s, q) sweep of Sec. 4.3 (Fig. 6): 64 pairs x 30 x 30 positions over the caustic on the planet's\n"
+           "side (workloads.fig6_sweep), rho = 1e-4; 4 random positions per pair (seed 620); oracle magnifications.")
+    _write("fig6_sweep.txt", hdr, ["index", "s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
+
+
 ALL = {"lightcurve_central": lightcurve_central, "central_wide": central_wide, "surrogate_queries": surrogate_queries,
        "map_planetary": map_planetary, "stress_resonant": stress_resonant, "batch_lightcurves": batch_lightcurves,
-       "paper_worked": paper_worked, "stress_resonant_1e4": stress_resonant_1e4}
+       "paper_worked": paper_worked, "stress_resonant_1e4": stress_resonant_1e4, "fig4_maps": fig4_maps, "lightcurve_orbital": lightcurve_orbital,
+       "fig6_sweep": fig6_sweep}
 
 if __name__ == "__main__":
     names = sys.argv[1:] or list(ALL)

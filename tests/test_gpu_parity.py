@@ -391,3 +391,54 @@ def test_autotuned_small_workload_chooses_warps(tmp_path, monkeypatch):
     # the cache file holds every shape tuned in this process; take the light curve's (work kind 1)
     line = [ln for ln in open(tmp_path / "tune.txt") if "prec=1;tol=1e-4;kind=1|" in ln][0].split("|")[1].split()
     assert len(line) == 5 and int(line[4]) in (1, 2, 4)
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_fig4_maps_full_grids_sampled(prec):
+    """The paper's three Fig. 4 speed maps (Sec. 4.1): each full 480 x 340 grid
+    in one launch, compared with the oracle at 128 random and 64 near-caustic
+    cells per map."""
+    rows = load("fig4_maps.txt")
+    for name in sorted(W.FIG4):
+        c = W.FIG4[name]
+        y1, y2 = W.fig4_grid(name)
+        mu = P.mag(c["s"], c["q"], c["rho"], dev(y1), dev(y2), rel_tol=1e-4, precision=prec).cpu().numpy()
+        sel = [r for r in rows if r[0] == name]
+        idx = np.array([int(r[1]) for r in sel])
+        ref = np.array([float(r[4]) for r in sel])
+        assert np.isfinite(mu).all() and (mu >= 1.0 - TOL).all()
+        assert rel_err(mu[idx], ref).max() <= TOL, (name, rel_err(mu[idx], ref).max())
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_fig6_sweep_sampled(prec):
+    """The (s, q) sweep of Sec. 4.3 (Fig. 6), 64 pairs x 900 positions with
+    per-position lenses in one launch, against the oracle at 4 positions of
+    every pair."""
+    S, Q, R, Y1, Y2 = W.fig6_sweep()
+    mu = P.mag_multi(dev(S), dev(Q), dev(R), dev(Y1), dev(Y2), rel_tol=1e-4, precision=prec).cpu().numpy()
+    rows = load("fig6_sweep.txt")
+    idx = np.array([int(r[0]) for r in rows])
+    ref = np.array([float(r[6]) for r in rows])
+    assert np.isfinite(mu).all()
+    assert rel_err(mu[idx], ref).max() <= TOL
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_lightcurve_orbital_motion(prec):
+    """An orbiting lens (separation and axis angle linear in time) on a
+    central-caustic trajectory, 200 points against the oracle; with zero rates
+    the orbital light curve equals the static one bit for bit."""
+    rows = load("lightcurve_orbital.txt")
+    t = np.array([float(r[0]) for r in rows])
+    ref = np.array([float(r[1]) for r in rows])
+    s, q, rho, u0, alpha, t0, tE = 1.0, 1e-3, 1e-3, 0.01, 1.0, 0.0, 20.0
+    mu = P.lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, 0.03, 0.2, dev(t), rel_tol=1e-4, precision=prec)
+    assert rel_err(mu.cpu().numpy(), ref).max() <= TOL
+    a = P.lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, 0.0, 0.0, dev(t), precision=prec).cpu().numpy()
+    b = P.lightcurve(s, q, rho, u0, alpha, t0, tE, dev(t), precision=prec).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    # a separation that turns non-positive gives NaN and the non-finite status
+    mu, err, ns, st = P.lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, 2.0, 0.0, np.array([-1.0, 0.0]),
+                                           details=True)
+    assert np.isnan(mu[0]) and (st[0] & P.POS_NONFINITE) and np.isfinite(mu[1])

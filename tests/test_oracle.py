@@ -323,3 +323,32 @@ def test_area_derivative_identity(s, q, rho, y1, y2):
     dg = (-g[3] + 8 * g[2] - 8 * g[1] + g[0]) / (12 * h * rho)
     mean = _limb_mean_point_mag(s, q, rho, y1, y2)
     assert abs(dg / (2 * rho * mean) - 1) < 1e-7
+
+
+def test_orbital_motion_point_lens_limit():
+    """Lens orbital motion (separation and axis angle linear in time): turning
+    the binary's axis only rotates the trajectory about the centre of mass, and
+    for a negligible companion (q = 1e-9) the primary sits there whatever the
+    separation, so the light curve is the single-lens finite-source curve at
+    u = sqrt(tau^2 + u0^2) -- here against the independent polygon integral
+    of the analytic point-lens images."""
+    s, q, rho, u0, alpha, t0, tE = 1.3, 1e-9, 0.05, 0.2, 0.7, 0.0, 10.0
+    t = np.array([-3.0, -1.0, 0.5, 2.5])
+    mu, st, _ = O.lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, 0.05, 0.3, t, scan_K=64)
+    assert (st == 0).all()
+    tau = (t - t0) / tE
+    ref = np.array([(4 * single_lens_polygon(u, rho, 1 << 16) - single_lens_polygon(u, rho, 1 << 15)) / 3
+                    for u in np.hypot(tau, u0)])
+    assert np.max(np.abs(mu / ref - 1)) < 1e-7
+
+
+def test_orbital_motion_mirror_symmetry():
+    """Reflecting the trajectory in the lens axis, (u0, alpha, dalpha/dt) ->
+    (-u0, -alpha, -dalpha/dt), maps y2 to -y2 at every time; the binary lens
+    is symmetric about its axis, so the light curve is unchanged."""
+    s, q, rho, u0, alpha, t0, tE, ds, da = 1.0, 0.1, 0.02, 0.05, 1.1, 0.0, 15.0, 0.02, 0.08
+    t = np.linspace(-2.0, 2.0, 7)
+    a, sa, _ = O.lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, ds, da, t, scan_K=64)
+    b, sb, _ = O.lightcurve_orbital(s, q, rho, -u0, -alpha, t0, tE, ds, -da, t, scan_K=64)
+    assert (sa == 0).all() and (sb == 0).all()
+    np.testing.assert_allclose(a, b, rtol=1e-10)
