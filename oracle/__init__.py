@@ -18,6 +18,7 @@ source; in short:
 * ``caustic``      -- critical curve J = 0 and its caustic image
 * ``trajectory``   -- straight-line source trajectory of a light curve
 * ``lightcurve_orbital`` -- light curve of a lens with linear orbital motion
+* ``mag_ld``       -- magnification of a linearly limb-darkened source
 * ``rayshoot``     -- brute-force inverse ray shooting (Sec. 1), for pinning ``mag``
 
 Per-position status codes from ``mag``: 0 ok, 1 crossing detectors disagree or
@@ -79,6 +80,10 @@ def _load():
         lib.orc_close_approaches.restype = ctypes.c_int
         lib.orc_mag.argtypes = [d, d, d, P, P, i64, ctypes.c_int, ctypes.c_int, P, P, P]
         lib.orc_mag.restype = ctypes.c_int
+        lib.orc_singular_radii.argtypes = [d, d, d, d, d, P, ctypes.c_int]
+        lib.orc_singular_radii.restype = ctypes.c_int
+        lib.orc_mag_radii.argtypes = [d, d, d, d, P, i64, ctypes.c_int, ctypes.c_int, P, P]
+        lib.orc_mag_radii.restype = ctypes.c_int
         lib.orc_trajectory.argtypes = [d, d, d, d, P, i64, P, P]
         lib.orc_trajectory.restype = None
         lib.orc_rayshoot.argtypes = [d, d, d, d, d, d, d, d, d, i64, i64, ctypes.c_int]
@@ -236,6 +241,95 @@ def lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, ds_dt, dalpha_dt, times, sc
 
 
 ORC_INPUT_STATUS = STATUS_INPUT
+
+
+def mag_radii(s: float, q: float, y1: float, y2: float, radii, scan_K: int = 0, nthreads: int = 0):
+    """Uniform-disc magnifications of one position for many radii (one caustic build)."""
+    r = np.ascontiguousarray(np.atleast_1d(radii), dtype=np.float64)
+    out = np.zeros(r.size)
+    st = np.zeros(r.size, np.int32)
+    if _load().orc_mag_radii(s, q, y1, y2, _ptr(r), r.size, scan_K, nthreads, _ptr(out), _ptr(st)):
+        raise ValueError("oracle: invalid lens")
+    return out, st
+
+
+def singular_radii(s: float, q: float, y1: float, y2: float, rmax: float) -> np.ndarray:
+    """Radii below rmax where a circle about (y1, y2) touches a fold of the
+    caustic or passes through a cusp (mu(r) is not smooth there)."""
+    out = np.zeros(256)
+    n = _load().orc_singular_radii(s, q, y1, y2, rmax, _ptr(out), 256)
+    if n < 0:
+        raise RuntimeError("oracle caustic failed")
+    return np.sort(out[: min(n, 256)])
+
+
+def mag_ld(s: float, q: float, rho: float, u: float, y1: float, y2: float, epsrel: float = 1e-9,
+           nthreads: int = 0):
+    """Magnification of a linearly limb-darkened disc, brightness
+    I(r) = 1 - u (1 - sqrt(1 - r^2/rho^2)), centred at (y1, y2).
+
+    The flux F = Int I dA_images is Int_0^rho I(r) dG(r) with G(r) = pi r^2
+    mu(r) the image area of a uniform disc of radius r; by parts and with
+    r = rho sin(phi),
+        mu_LD = [(1 - u) mu(rho) + u Int_0^{pi/2} sin^3(phi) mu(rho sin phi) dphi] / (1 - u/3),
+    evaluated with this oracle's uniform-disc magnification.  mu(r) is not
+    smooth where the circle of radius r touches the caustic (G - G_t ~
+    (r - r_t)^{3/2}), so the phi integral is cut at those radii
+    (singular_radii) and each piece is halved; on each half, phi = end +- D t^2
+    makes that behaviour smooth in t, and 16- and 24-point Gauss-Legendre
+    rules in t are compared; a piece whose two values differ by more than its
+    share of epsrel is halved again.
+    Returns (mu_LD, worst oracle status of the radii used)."""
+    xa, wa = np.polynomial.legendre.leggauss(16)
+    xb, wb = np.polynomial.legendre.leggauss(24)
+    xa, wa, xb, wb = 0.5 * (xa + 1), 0.5 * wa, 0.5 * (xb + 1), 0.5 * wb
+    cuts = [np.arcsin(min(r / rho, 1.0)) for r in singular_radii(s, q, y1, y2, rho)]
+    edges = [0.0]
+    for c in sorted(c for c in cuts if 1e-6 < c < 0.5 * np.pi - 1e-6):
+        if c - edges[-1] > 1e-6:  # cuts closer than that are one
+            edges.append(c)
+    edges = np.array(edges + [0.5 * np.pi])
+    pieces = list(zip(edges[:-1], edges[1:]))
+    mu_rho, st0 = mag_radii(s, q, y1, y2, [rho], nthreads=nthreads)
+    worst = int(st0[0])
+    done = 0.0
+
+    def halves(a, b):
+        m = 0.5 * (a + b)
+        return [(a, m - a, xa, wa, xb, wb), (b, m - b, xa, wa, xb, wb)]
+
+    for _ in range(30):
+        nodes, plan = [], []
+        for a, b in pieces:
+            for end, D, x1, w1, x2, w2 in halves(a, b):
+                i0 = len(nodes)
+                nodes += list(end + D * x1 * x1) + list(end + D * x2 * x2)
+                plan.append((abs(D), x1, w1, x2, w2, i0))
+        ph = np.array(nodes)
+        mu, st = mag_radii(s, q, y1, y2, rho * np.sin(ph), nthreads=nthreads)
+        worst = max(worst, int(st.max()))
+        f = np.sin(ph) ** 3 * mu
+        va, vb = [], []
+        for D, x1, w1, x2, w2, i0 in plan:
+            n1 = x1.size
+            va.append(D * np.sum(w1 * 2 * x1 * f[i0:i0 + n1]))
+            vb.append(D * np.sum(w2 * 2 * x2 * f[i0 + n1:i0 + n1 + x2.size]))
+        va = np.array(va).reshape(-1, 2).sum(1)
+        vb = np.array(vb).reshape(-1, 2).sum(1)
+        total = done + vb.sum()
+        width = np.array([b - a for a, b in pieces])
+        bad = np.abs(vb - va) > epsrel * abs(total) * (width / (0.5 * np.pi) + 1e-6)
+        done += vb[~bad].sum()
+        if not bad.any():
+            break
+        if 2 * bad.sum() + len(pieces) > 4096:
+            worst = max(worst, STATUS_QUAD)
+            done += vb[bad].sum()
+            break
+        pieces = [h for (pa, pb), keep in zip(pieces, bad) if keep for h in ((pa, 0.5 * (pa + pb)), (0.5 * (pa + pb), pb))]
+    else:
+        worst = max(worst, STATUS_QUAD)
+    return ((1.0 - u) * float(mu_rho[0]) + u * done) / (1.0 - u / 3.0), worst
 
 
 def rayshoot(s, q, rho, y1, y2, box, npix: int, nthreads: int = 0) -> float:

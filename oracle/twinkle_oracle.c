@@ -992,6 +992,91 @@ int orc_mag(double s, double q, double rho, const double *y1, const double *y2, 
     return 0;
 }
 
+/* Radii (below rmax, ascending, at most maxout; returns their number) at
+ * which the circle |zeta - zeta0| = r changes the way it meets the caustic,
+ * where the uniform-disc magnification mu(r) is not smooth: the local
+ * extrema of the distance from zeta0 along each caustic branch (the circle
+ * touches a fold there; refined by golden-section search on the branch
+ * parameter) and the distances of the cusps (where the caustic point stalls:
+ * a local minimum of its speed along the branch below a thousandth of the
+ * branch's median speed). */
+int orc_singular_radii(double s, double q, double y1, double y2, double rmax, double *out, int maxout) {
+    lens_t L = lens_make(s, q);
+    crit_t C;
+    const int M = 4096;
+    if (crit_build(&L, M, &C) != 0) { crit_free(&C); return -1; }
+    cplx z0 = cmk(y1, y2);
+    int n = 0;
+    real *d = (real *)malloc(sizeof(real) * M), *v = (real *)malloc(sizeof(real) * M), *vs = (real *)malloc(sizeof(real) * M);
+    if (!d || !v || !vs) { free(d); free(v); free(vs); crit_free(&C); return -1; }
+    for (int b = 0; b < 4; b++) {
+        /* the branch in order, continued through the wrap as crossings_caustic does */
+        cplx *zb = (cplx *)malloc(sizeof(cplx) * M);
+        for (int k = 0; k < M; k++) zb[k] = C.zc[4 * k + b];
+        for (int k = 0; k < M; k++) d[k] = c_abs(lens_map(&L, zb[k]) - z0);
+        for (int k = 0; k + 1 < M; k++) v[k] = c_abs(lens_map(&L, zb[k + 1]) - lens_map(&L, zb[k]));
+        v[M - 1] = v[M - 2];
+        for (int k = 0; k < M; k++) vs[k] = v[k];
+        for (int i = 1; i < M; i++) /* median speed: insertion sort of a copy */
+            for (int k = i; k > 0 && vs[k] < vs[k - 1]; k--) { real t = vs[k]; vs[k] = vs[k - 1]; vs[k - 1] = t; }
+        const real vmed = vs[M / 2];
+        for (int k = 1; k + 1 < M; k++) {
+            const real pa = TWO_PI_L * (k - 1) / M, pb = TWO_PI_L * (k + 1) / M;
+            if ((d[k] - d[k - 1]) * (d[k + 1] - d[k]) < 0 && n < maxout) {
+                /* extremum of the distance: golden-section search */
+                const real sg = d[k] < d[k - 1] ? 1.0 : -1.0; /* minimise sg * d */
+                real lo = pa, hi = pb;
+                const real gr = 0.6180339887498948482;
+                real x1 = hi - gr * (hi - lo), x2 = lo + gr * (hi - lo);
+                cplx g1 = crit_point(&L, x1, zb[k]), g2 = crit_point(&L, x2, zb[k]);
+                real f1 = sg * c_abs(lens_map(&L, g1) - z0), f2 = sg * c_abs(lens_map(&L, g2) - z0);
+                for (int it = 0; it < 90 && hi - lo > 1e-30; it++) {
+                    if (f1 < f2) { hi = x2; x2 = x1; f2 = f1; x1 = hi - gr * (hi - lo); g1 = crit_point(&L, x1, zb[k]); f1 = sg * c_abs(lens_map(&L, g1) - z0); }
+                    else { lo = x1; x1 = x2; f1 = f2; x2 = lo + gr * (hi - lo); g2 = crit_point(&L, x2, zb[k]); f2 = sg * c_abs(lens_map(&L, g2) - z0); }
+                }
+                const real r = sg * (f1 < f2 ? f1 : f2);
+                if (r < rmax) out[n++] = (double)r;
+            }
+            if (v[k] < v[k - 1] && v[k] <= v[k + 1] && v[k] < 1e-3 * vmed && n < maxout) {
+                const real r = c_abs(lens_map(&L, zb[k]) - z0); /* a cusp */
+                if (r < rmax) out[n++] = (double)r;
+            }
+        }
+        free(zb);
+    }
+    free(d); free(v); free(vs);
+    crit_free(&C);
+    for (int i = 1; i < n; i++)
+        for (int k = i; k > 0 && out[k] < out[k - 1]; k--) { double t = out[k]; out[k] = out[k - 1]; out[k - 1] = t; }
+    return n;
+}
+
+/* Uniform-disc magnifications of one source position for n radii (the caustic
+ * is built once): the annuli of a limb-darkened source.  status[i] as in
+ * orc_mag.  Returns 0, or ORC_INPUT. */
+int orc_mag_radii(double s, double q, double y1, double y2, const double *radii, int64_t n, int scan_K, int nthreads,
+                  double *out, int32_t *status) {
+    if (!(s > 0) || !(q > 0) || n < 0) return ORC_INPUT;
+    lens_t L = lens_make(s, q);
+    crit_t C;
+    if (crit_build(&L, 4096, &C) != 0) {
+        crit_free(&C);
+        for (int64_t i = 0; i < n; i++) { out[i] = NAN; if (status) status[i] = ORC_ROOT; }
+        return 0;
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < n; i++) {
+        mag_info_t info;
+        out[i] = radii[i] > 0 ? (double)mag_one(&L, &C, y1, y2, radii[i], scan_K, &info) : NAN;
+        if (status) status[i] = radii[i] > 0 ? info.status : ORC_INPUT;
+    }
+    crit_free(&C);
+    return 0;
+}
+
 /* Source trajectory of a light curve (a straight line; the paper leaves the
  * convention open): tau = (t - t0)/tE,
  *   y1 = tau cos(alpha) - u0 sin(alpha),  y2 = tau sin(alpha) + u0 cos(alpha). */

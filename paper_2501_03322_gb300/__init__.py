@@ -78,6 +78,8 @@ def lib():
             L.tw_lightcurve.restype = I
             L.tw_lightcurve_ex.argtypes = [d, d, d, d, d, d, d, P, i64, d, P, P]
             L.tw_lightcurve_ex.restype = I
+            L.tw_mag_ld.argtypes = [d, d, d, d, P, P, i64, d, P, P]
+            L.tw_mag_ld.restype = I
             L.tw_lightcurve_orbital.argtypes = [d, d, d, d, d, d, d, d, d, P, i64, d, P, P]
             L.tw_lightcurve_orbital.restype = I
             L.tw_mag_multi.argtypes = [P, P, P, P, P, i64, d, P, P]
@@ -301,6 +303,23 @@ def mag(s, q, rho, y1, y2, rel_tol=1e-4, precision=PREC_FP64, samples_per_iter=6
     o = make_opts(precision, samples_per_iter, max_samples, _stream_of(y1, stream), err, nsamp, status, autotune,
                   use_graph, warps_per_position)
     _check(lib().tw_mag_ex(s, q, rho, _ptr(y1), _ptr(y2), n, rel_tol, _ptr(out), ctypes.byref(o)))
+    return (out, err, nsamp, status) if details else out
+
+
+def mag_ld(s, q, rho, u, y1, y2, rel_tol=1e-4, precision=PREC_FP64, max_samples=4096, out=None, details=False,
+           stream=None):
+    """Magnification of linearly limb-darkened sources (tw_mag_ld), brightness 1 - u (1 - sqrt(1 - r^2/rho^2))."""
+    y1, y2 = _prep(y1), _prep(y2)
+    n = int(y1.shape[0])
+    if out is None:
+        out = _alloc_like(y1, n, np.float64, "float64")
+    err = nsamp = status = None
+    if details:
+        err = _alloc_like(y1, n, np.float64, "float64")
+        nsamp = _alloc_like(y1, n, np.int32, "int32")
+        status = _alloc_like(y1, n, np.int8, "int8")
+    o = make_opts(precision, 64, max_samples, _stream_of(y1, stream), err, nsamp, status)
+    _check(lib().tw_mag_ld(s, q, rho, u, _ptr(y1), _ptr(y2), n, rel_tol, _ptr(out), ctypes.byref(o)))
     return (out, err, nsamp, status) if details else out
 
 

@@ -66,6 +66,8 @@ struct DevState {
     char *calib = nullptr;          // outputs of autotuning calibration runs
     size_t calib_bytes = 0;
     cudaGraphExec_t graph = nullptr;  // replayable {counter reset, persistent kernel}
+    char *ld = nullptr;             // node scratch of the limb-darkening kernel
+    size_t ld_bytes = 0;
     char name[256] = {0};           // device name (autotune cache key)
 };
 
@@ -171,6 +173,11 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     }
     const bool occ4 = w == 1 && (cfg.occ4 > 0 || (cfg.occ4 < 0 && src.kind == 3));
     pick_kernel(prec, cfg.spl, occ4, w, &lf, &of);
+    if (src.kind == 5) {  // limb-darkened sources: their own kernel, one warp per source
+        w = 1;
+        if (prec == 0) { lf = launch_ld_0; of = occupancy_ld_0; }
+        else { lf = launch_ld_1; of = occupancy_ld_1; }
+    }
     int occ = 0;
     cudaError_t e = of(&occ);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -184,6 +191,8 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     const size_t slot_bytes = arena_slot_bytes(cap);
     int rc = grow(&d.arena, &d.arena_bytes, slot_bytes * (size_t)blocks * WPB);
     if (rc) return rc;
+    if (src.kind == 5 && (rc = grow(&d.ld, &d.ld_bytes, (size_t)blocks * WPB * LD_WARP_DOUBLES * sizeof(double))))
+        return rc;
     // repair queue: room for every work item up to 2^20 (positions beyond it
     // that fail the slope test keep the main pass's result and PS_SLOPE)
     const size_t relist_cap = (size_t)(src.n < (1 << 20) ? (src.n > 0 ? src.n : 1) : (1 << 20));
@@ -204,6 +213,7 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     kp.counter = d.counter;
     kp.relist = d.relist;
     kp.relist_cap = d.relist_bytes / sizeof(int64_t);
+    kp.ld = (double *)d.ld;
     // main pass, then the repair pass over the items it queued (usually none:
     // the repair kernel finds an empty queue and exits)
     auto kernels = [&]() -> cudaError_t {
@@ -410,7 +420,7 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     if (dev) {
         for (int i = 0; i < c.nin; i++) din[i] = c.in[i];
         WorkSrc src = bind(din);
-        if (o.autotune && (rc = autotune(d, src, tol, o.precision, o.max_samples, st, &cfg))) return rc;
+        if (o.autotune && src.kind != 5 && (rc = autotune(d, src, tol, o.precision, o.max_samples, st, &cfg))) return rc;
         return launch(d, src, tol, o.precision, o.max_samples, cfg, o.use_graph != 0, out, o.err_out, o.nsamp_out,
                       o.pos_status, st);
     }
@@ -435,7 +445,7 @@ static int run_call(const Call &c, double tol, const tw_opts *opts_in, double *o
     double *derr = o.err_out ? (double *)(d.stage + o_err) : nullptr;
     int32_t *dns = o.nsamp_out ? (int32_t *)(d.stage + o_ns) : nullptr;
     int8_t *dps = (int8_t *)(d.stage + o_ps);
-    if (o.autotune && (rc = autotune(d, src, tol, o.precision, o.max_samples, st, &cfg))) return rc;
+    if (o.autotune && src.kind != 5 && (rc = autotune(d, src, tol, o.precision, o.max_samples, st, &cfg))) return rc;
     if ((rc = launch(d, src, tol, o.precision, o.max_samples, cfg, o.use_graph != 0, dout, derr, dns, dps, st)))
         return rc;
     int8_t *hps = o.pos_status;
@@ -507,6 +517,27 @@ int tw_mag_ex(double s, double q, double rho, const double *y1, const double *y2
         WorkSrc w;
         memset(&w, 0, sizeof(w));
         w.kind = 0; w.n = n; w.s = s; w.q = q; w.rho = rho; w.stride = 1;
+        w.y1 = (const double *)din[0];
+        w.y2 = (const double *)din[1];
+        return w;
+    });
+}
+
+int tw_mag_ld(double s, double q, double rho, double u, const double *y1, const double *y2, int64_t n,
+              double rel_tol, double *out, const tw_opts *opts) {
+    if (n < 0 || !finite_pos(s) || !finite_pos(q) || !finite_pos(rho) || !finite_pos(rel_tol) || !isfinite(u) ||
+        u < 0.0 || u > 1.0)
+        return TW_EINVAL;
+    if (n > 0 && (!y1 || !y2 || !out)) return TW_EINVAL;
+    Call c;
+    c.nin = 2;
+    c.in[0] = y1; c.insz[0] = (size_t)n * 8;
+    c.in[1] = y2; c.insz[1] = (size_t)n * 8;
+    c.n = n;
+    return run_call(c, rel_tol, opts, out, [&](const void **din) {
+        WorkSrc w;
+        memset(&w, 0, sizeof(w));
+        w.kind = 5; w.n = n; w.s = s; w.q = q; w.rho = rho; w.stride = 1; w.ld_u = u;
         w.y1 = (const double *)din[0];
         w.y2 = (const double *)din[1];
         return w;

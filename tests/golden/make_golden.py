@@ -19,6 +19,8 @@ Files (text, one position per line: inputs, mu, oracle status):
   central_wide.txt        4096 centres on the central caustic of a wide planetary lens
   lightcurve_orbital.txt  200 points of a central-caustic light curve of an orbiting lens (separation
                           and axis angle linear in time)
+  limb_darkened.txt       32 positions of linearly limb-darkened sources (u = 0.6): 16 whose limb crosses a
+                          caustic (central-caustic light curve, planetary-caustic map) and 16 that do not
   fig4_maps.txt           the paper's three Fig. 4 grids (480 x 340, q = 1e-4): per map 128
                           random cells and 64 cells within rho of the caustic
   fig6_sweep.txt          the (s, q) sweep (64 pairs x 30 x 30, rho = 1e-4): 4 random positions
@@ -252,6 +254,47 @@ def lightcurve_orbital():
     _write("lightcurve_orbital.txt", hdr, ["t", "mu", "status", "ncross"], zip(t, mu, st, nx))
 
 
+LD_U = 0.6
+
+
+def limb_darkened():
+    """Limb-darkened sources (linear law, u = 0.6) on two lenses: positions of
+    the central-caustic light curve and of the planetary-caustic map, half of
+    them crossing a caustic (oracle ncross >= 2)."""
+    jobs = []
+    lc = [ln.split() for ln in open(os.path.join(HERE, "lightcurve_central.txt")) if not ln.startswith("#")]
+    c = W.LIGHTCURVE_CENTRAL
+    t = np.array([float(r[0]) for r in lc])
+    nx = np.array([int(r[3]) for r in lc])
+    rng = np.random.default_rng(700)
+    pick = np.r_[rng.choice(np.nonzero(nx >= 2)[0], 8, replace=False), rng.choice(np.nonzero(nx < 2)[0], 8, replace=False)]
+    y1, y2 = O.trajectory(c["u0"], c["alpha"], c["t0"], c["tE"], t[pick])
+    jobs += [("lightcurve_central", c["s"], c["q"], c["rho"], a, b) for a, b in zip(y1, y2)]
+    mp = [ln.split() for ln in open(os.path.join(HERE, "map_planetary.txt")) if not ln.startswith("#")]
+    m = W.MAP_PLANETARY
+    xr = [r for r in mp if int(r[5]) >= 2]
+    sr = [r for r in mp if int(r[5]) < 2]
+    for r in [xr[i] for i in rng.choice(len(xr), 8, replace=False)] + [sr[i] for i in rng.choice(len(sr), 8, replace=False)]:
+        jobs.append(("map_planetary", m["s"], m["q"], m["rho"], float(r[1]), float(r[2])))
+
+    def run(j):
+        tag, s, q, rho, a, b = j
+        mu, st = O.mag_ld(s, q, rho, LD_U, a, b, epsrel=1e-8, nthreads=0)
+        nxr = len(O.crossings(s, q, rho, a, b))
+        return (tag, s, q, rho, LD_U, a, b, mu, st, nxr)
+
+    rows = [run(j) for j in jobs]  # each position uses every core over its radii
+    path = os.path.join(HERE, "limb_darkened.txt")
+    with open(path, "w") as f:
+        f.write("# Linearly limb-darkened sources, I(r) = 1 - u (1 - sqrt(1 - r^2/rho^2)), u = 0.6: 16 positions of\n")
+        f.write("# the central-caustic light curve and 16 cells of the planetary-caustic map (seed 700), half of each\n")
+        f.write("# crossing a caustic; oracle magnifications (oracle.mag_ld, adaptive in the annulus radius).\n")
+        f.write("# columns: set s q rho u y1 y2 mu status ncross\n")
+        for r in rows:
+            f.write("%s %r %r %r %r %r %r %r %d %d\n" % (r[0], r[1], r[2], r[3], r[4], float(r[5]), float(r[6]), float(r[7]), int(r[8]), int(r[9])))
+    print("wrote", path, len(rows), "rows")
+
+
 def fig4_maps():
     rows = []
     for k, name in enumerate(sorted(W.FIG4)):
@@ -298,6 +341,7 @@ def fig6_sweep():
 ALL = {"lightcurve_central": lightcurve_central, "central_wide": central_wide, "surrogate_queries": surrogate_queries,
        "map_planetary": map_planetary, "stress_resonant": stress_resonant, "batch_lightcurves": batch_lightcurves,
        "paper_worked": paper_worked, "stress_resonant_1e4": stress_resonant_1e4, "fig4_maps": fig4_maps, "lightcurve_orbital": lightcurve_orbital,
+       "limb_darkened": limb_darkened,
        "fig6_sweep": fig6_sweep}
 
 if __name__ == "__main__":

@@ -442,3 +442,26 @@ def test_lightcurve_orbital_motion(prec):
     mu, err, ns, st = P.lightcurve_orbital(s, q, rho, u0, alpha, t0, tE, 2.0, 0.0, np.array([-1.0, 0.0]),
                                            details=True)
     assert np.isnan(mu[0]) and (st[0] & P.POS_NONFINITE) and np.isfinite(mu[1])
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_limb_darkened_sources(prec):
+    """Linearly limb-darkened sources (u = 0.6) on the central-caustic and the
+    planetary-caustic lenses, half of them crossing a caustic, against the
+    oracle; u = 0 reproduces the uniform disc within the tolerance."""
+    rows = load("limb_darkened.txt")
+    for tag in ("lightcurve_central", "map_planetary"):
+        sel = [r for r in rows if r[0] == tag]
+        s, q, rho, u = (float(sel[0][k]) for k in (1, 2, 3, 4))
+        y1 = np.array([float(r[5]) for r in sel])
+        y2 = np.array([float(r[6]) for r in sel])
+        ref = np.array([float(r[7]) for r in sel])
+        mu, err, ns, st = P.mag_ld(s, q, rho, u, dev(y1), dev(y2), rel_tol=TOL, precision=prec, details=True)
+        mu, err = mu.cpu().numpy(), err.cpu().numpy()
+        e = rel_err(mu, ref)
+        assert e.max() <= TOL, (tag, e.max(), int(np.argmax(e)))
+        print("limb-darkened %s (%s): max rel err %.2e, estimate bounds the error on %d of %d" % (
+            tag, "fp64" if prec == P.PREC_FP64 else "mixed", e.max(), int((np.abs(mu - ref) <= err).sum()), len(sel)))
+        m0 = P.mag_ld(s, q, rho, 0.0, dev(y1), dev(y2), rel_tol=TOL, precision=prec).cpu().numpy()
+        m1 = P.mag(s, q, rho, dev(y1), dev(y2), rel_tol=TOL, precision=prec).cpu().numpy()
+        assert rel_err(m0, m1).max() <= 2 * TOL

@@ -352,3 +352,46 @@ def test_orbital_motion_mirror_symmetry():
     b, sb, _ = O.lightcurve_orbital(s, q, rho, -u0, -alpha, t0, tE, ds, -da, t, scan_K=64)
     assert (sa == 0).all() and (sb == 0).all()
     np.testing.assert_allclose(a, b, rtol=1e-10)
+
+
+def _ld_profile(r, rho, u):
+    return 1.0 - u * (1.0 - np.sqrt(np.clip(1.0 - (r / rho) ** 2, 0.0, None)))
+
+
+def _point_mag(d):
+    return (d * d + 2.0) / (d * np.sqrt(d * d + 4.0))
+
+
+@pytest.mark.parametrize("rho,u", [(0.1, 0.6), (0.01, 0.3), (0.5, 1.0)])
+def test_limb_darkening_centred_point_lens(rho, u):
+    """A limb-darkened disc centred on a point lens (negligible companion):
+    the definition mu = Int I mu_ps dA / Int I dA with the analytic point-lens
+    magnification (r^2 + 2)/(r sqrt(r^2 + 4)) at distance r, as a 1-D radial
+    integral -- no contour, no annuli."""
+    from scipy.integrate import quad
+
+    s, q = 10.0, 1e-9
+    x1 = -q * s / (1 + q)
+    num = quad(lambda r: _ld_profile(r, rho, u) * _point_mag(r) * 2 * np.pi * r, 0.0, rho, epsrel=1e-12,
+               limit=200)[0]
+    den = np.pi * rho * rho * (1.0 - u / 3.0)
+    mu, st = O.mag_ld(s, q, rho, u, x1, 0.0)
+    assert st == 0
+    assert abs(mu / (num / den) - 1) < 1e-8
+
+
+def test_limb_darkening_off_centre_point_lens():
+    """Off-centre limb-darkened disc on a point lens: the definition as a 2-D
+    integral over the disc in polar coordinates about its centre, with the
+    analytic point-lens magnification; and u = 0 gives the uniform disc."""
+    from scipy.integrate import dblquad
+
+    s, q, rho, u, d = 10.0, 1e-9, 0.2, 0.7, 0.3
+    x1 = -q * s / (1 + q)
+    f = lambda th, r: _ld_profile(r, rho, u) * _point_mag(np.hypot(d + r * np.cos(th), r * np.sin(th))) * r
+    num = dblquad(f, 0.0, rho, 0.0, 2 * np.pi, epsabs=0.0, epsrel=1e-10)[0]
+    den = np.pi * rho * rho * (1.0 - u / 3.0)
+    mu, st = O.mag_ld(s, q, rho, u, x1 + d, 0.0)
+    assert st == 0 and abs(mu / (num / den) - 1) < 1e-7
+    m0, _ = O.mag_ld(1.0, 0.1, 0.05, 0.0, 0.1, 0.05)
+    assert abs(m0 / O.mag(1.0, 0.1, 0.05, [0.1], [0.05])[0][0] - 1) < 1e-12
