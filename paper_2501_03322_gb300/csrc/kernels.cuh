@@ -220,19 +220,244 @@ __global__ void __launch_bounds__(TPB, OCC) contour_kernel(KParams kp) {
 //   mu_LD = [(1 - u) mu(rho) + u Int_0^{pi/2} h(phi) dphi] / (1 - u/3),
 //   h(phi) = sin^3(phi) mu(rho sin phi),
 // mu(r) being the magnification of a uniform disc of radius r (the contour
-// integral of integrate_position).  h has kinks where the circle of radius r
-// touches the caustic, so the phi integral is adaptive Simpson: panels of
-// five equally spaced nodes, four of width pi/8 to start (16 radii; h(0) =
-// 0), each valued by the two half-panel Simpson rules with the Richardson
-// correction, its error |S(panel) - S(halves)| / 15; a panel above its share
-// of half the tolerance is split in two (four new radii), up to LD_MAXP
-// panels.  Each uniform disc is integrated to the other half of the
-// tolerance.  One warp per source; the panels live in a per-warp global
-// scratch managed by lane 0.
-constexpr int LD_MAXP = 24;       // panels
-constexpr int LD_PSTRIDE = 7;     // a, w, h[5] per panel
+// integral of integrate_position).
+//
+// mu(r) is not smooth where the circle of radius r about the source centre
+// touches a fold of the caustic or passes over a cusp: as the circle starts
+// to cut into a fold, the limb integral of the point-source magnification
+// (which grows as 1/sqrt(distance) inside the fold) tends to a non-zero
+// constant, so d(image area)/dr jumps.  Those radii are the stationary points
+// of the distance from the centre along the caustic (ld_cuts).  The phi
+// integral is cut there, and on each piece phi = a + (b - a) tau(t) with
+// tau' = 0 at the cut ends, which makes the kinks smooth in t:
+// tau = 3t^2 - 2t^3 (cuts at both ends), t^2 (left), 2t - t^2 (right), t
+// (none).  The t integrals are adaptive Simpson: panels of five equally
+// spaced nodes, one per piece and at least four in all to start, each valued
+// by its two half-panel Simpson rules with the Richardson correction, its
+// error |S(panel) - S(halves)| / 15 (valid now that the integrand is smooth);
+// a panel above its share of half the tolerance is split in two (four new
+// radii), up to LD_MAXP panels.  Each uniform disc is integrated to the other
+// half of the tolerance.  One warp per source; the panels live in a per-warp
+// global scratch managed by lane 0.
+constexpr int LD_MAXP = 40;       // panels
+constexpr int LD_PSTRIDE = 8;     // piece, t0, w, h[5] per panel
 constexpr int LD_SPLIT = 4;       // panel splits per round
-constexpr int LD_WARP_DOUBLES = LD_MAXP * LD_PSTRIDE + 2 * LD_MAXP + 8 * LD_SPLIT;
+constexpr int LD_NPHI = 512;      // angles of the critical-curve sweep (16 per lane)
+constexpr int LD_MAXCUT = 16;     // cut radii kept per source
+constexpr int LD_LANECUT = 4;     // cut radii found per lane
+constexpr int LD_WARP_DOUBLES = LD_MAXP * LD_PSTRIDE + 2 * LD_MAXP + 8 * LD_SPLIT + LD_MAXCUT + 2;
+
+// Critical curve (J = 0, Eq. 7) in the secondary's frame, parameterised by
+// the phase phi of f'(z): e^{i phi} eta^2 (eta + s)^2 = m1 eta^2 + m2 (eta + s)^2,
+// a quartic in eta (m1 + m2 = 1).
+__device__ __forceinline__ void crit_coeffs_f(float s, float m2, float ph, cxf c[5]) {
+    float sn, cs;
+    sincosf(ph, &sn, &cs);
+    c[4] = {cs, sn};
+    c[3] = {2.0f * s * cs, 2.0f * s * sn};
+    c[2] = {s * s * cs - 1.0f, s * s * sn};
+    c[1] = {-2.0f * s * m2, 0.0f};
+    c[0] = {-m2 * s * s, 0.0f};
+}
+
+// Aberth-Ehrlich iteration on the quartic c (FP32), from z.  Warm-started
+// from the previous angle, each root index stays on one branch.
+__device__ __forceinline__ void crit_aberth_f(const cxf c[5], cxf z[4], int maxit) {
+    for (int it = 0; it < maxit; it++) {
+        cxf S4[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) S4[a] = {0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = a + 1; b < 4; b++) {
+                const cxf r = inv(z[a] - z[b]);
+                S4[a] = S4[a] + r;
+                S4[b] = S4[b] - r;
+            }
+        float wmax = 0.f, zmax = 0.f;
+        cxf w[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            cxf p = c[4], d = {0.f, 0.f};
+#pragma unroll
+            for (int t = 3; t >= 0; t--) {
+                d = cmad(d, z[a], p);
+                p = cmad(p, z[a], c[t]);
+            }
+            w[a] = cdiv(p, d - p * S4[a]);
+            wmax = fmaxf(wmax, norm2(w[a]));
+            zmax = fmaxf(zmax, norm2(z[a]));
+        }
+#pragma unroll
+        for (int a = 0; a < 4; a++) z[a] = z[a] - w[a];
+        if (wmax <= 1e-12f * (zmax + 1e-30f)) break;
+    }
+}
+
+// Newton steps on the critical-curve quartic at angle ph (FP64) from eta.
+__device__ __forceinline__ cxd crit_newton(double s, double m2, double ph, cxd eta, int steps) {
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    const cxd e = {cs, sn};
+    for (int k = 0; k < steps; k++) {
+        const cxd ep = {eta.x + s, eta.y};
+        const cxd Q = (eta * eta) * (ep * ep);
+        const cxd Qp = 2.0 * (eta * ep * cxd{2.0 * eta.x + s, 2.0 * eta.y});
+        const cxd R = {eta.x * eta.x - eta.y * eta.y + 2.0 * m2 * s * eta.x + m2 * s * s,
+                       2.0 * eta.x * eta.y + 2.0 * m2 * s * eta.y};
+        const cxd Rp = {2.0 * eta.x + 2.0 * m2 * s, 2.0 * eta.y};
+        eta = eta - cdiv(e * Q - R, e * Qp - Rp);
+    }
+    return eta;
+}
+
+// Caustic point zeta = eta - conj(g(eta)) of the critical point eta at angle
+// e = e^{i phi}, and D = Re(conj(zeta - y0) dzeta/dphi): the derivative of
+// |zeta - y0|^2 / 2 along the branch.  dzeta/dphi = eta' - conj(g' eta'),
+// eta' = -i R / (e Q' - R') by implicit differentiation of the quartic
+// (e Q = R on the curve).  Returns zeta.
+template <typename T>
+__device__ __forceinline__ cx<T> caustic_point(T s, T m1, T m2, cx<T> e, cx<T> eta, cx<T> y0, T &D) {
+    const cx<T> ep = {eta.x + s, eta.y};
+    const cx<T> i1 = inv(ep), i2 = inv(eta);
+    const cx<T> g = m1 * i1 + m2 * i2;
+    const cx<T> gp = T(-1) * (m1 * (i1 * i1) + m2 * (i2 * i2));
+    const cx<T> R = m1 * (eta * eta) + m2 * (ep * ep);
+    const cx<T> Qp = T(2) * (eta * ep * cx<T>{T(2) * eta.x + s, T(2) * eta.y});
+    const cx<T> Rp = {T(2) * eta.x + T(2) * m2 * s, T(2) * eta.y};
+    const cx<T> etap = cdiv(cx<T>{R.y, -R.x}, e * Qp - Rp);
+    const cx<T> zeta = eta - conj(g);
+    const cx<T> zp = etap - conj(gp * etap);
+    D = dot(zeta - y0, zp);
+    return zeta;
+}
+
+// Radii below rho at which the circle about the source centre y0 (secondary
+// frame) touches the caustic or passes over a cusp: the stationary points of
+// |zeta_c - y0| along each of the four branches of the caustic (at a cusp
+// dzeta/dphi vanishes, so cusps are among them).  The critical curve is swept
+// at LD_NPHI angles in FP32, LD_NPHI/32 consecutive angles per lane with
+// warm-started roots; a sign change of D between neighbouring angles whose
+// caustic points come within rho (plus the chord between them) of y0 is
+// bisected in FP64 (Newton-polished roots).  Writes the radii, ascending, to
+// cut[0..n) (warp scratch) and returns n (every lane).
+static __device__ __noinline__ int ld_cuts(const LensK &L, double rho, double *cut) {
+    const int lane = threadIdx.x & 31;
+    constexpr int PER = LD_NPHI / 32;
+    const double dphi = 6.283185307179586 / LD_NPHI;
+    const float sf = (float)L.s, m1f = (float)L.m1, m2f = (float)L.m2, rhof = (float)rho;
+    const cxf y0f = to_f(L.y0);
+    cxf z[4], c[5];
+    const float r0 = 1.0f + sf;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float sn, cs;
+        sincosf(1.5707963f * k + 0.3f, &sn, &cs);
+        z[k] = {-0.5f * sf + r0 * cs, r0 * sn};
+    }
+    const int j0 = PER * lane;
+    crit_coeffs_f(sf, m2f, (float)(dphi * j0), c);
+    crit_aberth_f(c, z, 200);
+    float Dp[4];
+    cxf cp[4], zprev[4];
+    {
+        float sn, cs;
+        sincosf((float)(dphi * j0), &sn, &cs);
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            cp[a] = caustic_point<float>(sf, m1f, m2f, cxf{cs, sn}, z[a], y0f, Dp[a]);
+            zprev[a] = z[a];
+        }
+    }
+    double found[LD_LANECUT];
+    int nf = 0;
+    for (int j = 1; j <= PER; j++) {
+        const double ph = dphi * (j0 + j);
+        crit_coeffs_f(sf, m2f, (float)ph, c);
+        crit_aberth_f(c, z, 60);
+        float sn, cs;
+        sincosf((float)ph, &sn, &cs);
+#pragma unroll 1
+        for (int a = 0; a < 4; a++) {
+            float Dn;
+            const cxf cn = caustic_point<float>(sf, m1f, m2f, cxf{cs, sn}, z[a], y0f, Dn);
+            const float chord = sqrtf(norm2(cn - cp[a]));
+            const float dmin = sqrtf(fminf(norm2(cn - y0f), norm2(cp[a] - y0f)));
+            if ((Dn > 0.f) != (Dp[a] > 0.f) && dmin < 1.01f * rhof + chord && nf < LD_LANECUT) {
+                // bisect the sign change in FP64
+                double lo = ph - dphi, hi = ph;
+                cxd zl = crit_newton(L.s, L.m2, lo, to_d(zprev[a]), 4);
+                double Dl;
+                {
+                    double sl, cl;
+                    sincos(lo, &sl, &cl);
+                    caustic_point<double>(L.s, L.m1, L.m2, cxd{cl, sl}, zl, L.y0, Dl);
+                }
+                for (int b = 0; b < 32; b++) {
+                    const double mid = 0.5 * (lo + hi);
+                    const cxd zm = crit_newton(L.s, L.m2, mid, zl, 3);
+                    double sm, cm, Dm;
+                    sincos(mid, &sm, &cm);
+                    caustic_point<double>(L.s, L.m1, L.m2, cxd{cm, sm}, zm, L.y0, Dm);
+                    if ((Dm > 0.0) == (Dl > 0.0)) {
+                        lo = mid;
+                        zl = zm;
+                        Dl = Dm;
+                    } else {
+                        hi = mid;
+                    }
+                }
+                double sl, cl, Dx;
+                sincos(lo, &sl, &cl);
+                const cxd zc = caustic_point<double>(L.s, L.m1, L.m2, cxd{cl, sl}, zl, L.y0, Dx);
+                const double d = sqrt(norm2(zc - L.y0));
+                if (d < rho && isfinite(d)) found[nf++] = d;
+            }
+            Dp[a] = Dn;
+            cp[a] = cn;
+            zprev[a] = z[a];
+        }
+    }
+    // gather: exclusive prefix sum of the lanes' counts
+    int off = nf;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, off, o);
+        if (lane >= o) off += t;
+    }
+    const int total = __shfl_sync(FULL, off, 31);
+    off -= nf;
+    for (int k = 0; k < nf; k++)
+        if (off + k < LD_MAXCUT) cut[off + k] = found[k];
+    __syncwarp();
+    const int n = total < LD_MAXCUT ? total : LD_MAXCUT;
+    if (lane == 0)
+        for (int i = 1; i < n; i++) {  // insertion sort
+            const double v = cut[i];
+            int k = i - 1;
+            while (k >= 0 && cut[k] > v) {
+                cut[k + 1] = cut[k];
+                k--;
+            }
+            cut[k + 1] = v;
+        }
+    __syncwarp();
+    return n;
+}
+
+// Node of piece i at t: phi and the factor (b - a) tau'(t) (see above).
+__device__ __forceinline__ double ld_map(const double *ed, int npc, int i, double t, double &jac) {
+    const double a = ed[i], b = ed[i + 1], w = b - a;
+    const bool lc = i > 0, rc = i < npc - 1;
+    double tau, dt;
+    if (lc && rc) { tau = t * t * (3.0 - 2.0 * t); dt = 6.0 * t * (1.0 - t); }
+    else if (lc) { tau = t * t; dt = 2.0 * t; }
+    else if (rc) { tau = t * (2.0 - t); dt = 2.0 * (1.0 - t); }
+    else { tau = t; dt = 1.0; }
+    jac = w * dt;
+    return t == 1.0 ? b : a + w * tau;
+}
 
 template <int PREC>
 __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) ld_kernel(KParams kp) {
@@ -245,16 +470,16 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) ld_kernel(KParams kp)
     co.bar = 0;
     const int gw = blockIdx.x * WPB + wib;
     const Arena ar = arena_at(kp.arena, kp.slot_bytes, kp.cap, gw);
-    double *pn = kp.ld + (size_t)gw * LD_WARP_DOUBLES;  // panels: a, w, h[0..4]
+    double *pn = kp.ld + (size_t)gw * LD_WARP_DOUBLES;  // panels: piece, t0, w, h[0..4]
     double *pe = pn + LD_MAXP * LD_PSTRIDE;             // per panel: propagated disc error, Simpson error
-    double *sp = pe + 2 * LD_MAXP;                      // this round's new nodes: angle, h, disc error, target
+    double *sp = pe + 2 * LD_MAXP;                      // this round's new nodes (t) and the panel they split
+    double *ed = sp + 8 * LD_SPLIT;                     // piece edges in phi (cut radii first)
     const double halfpi = 1.5707963267948966192, u = kp.src.ld_u;
     const double tol_u = 0.5 * kp.tol;  // each uniform disc; the other half for the phi integral
-    unsigned long long it = 0;
     for (;;) {
         unsigned long long first = 0;
         if (lane == 0) first = atomicAdd(kp.counter, 1ull);
-        it = __shfl_sync(FULL, first, 0);
+        const unsigned long long it = __shfl_sync(FULL, first, 0);
         if (it >= (unsigned long long)kp.src.n) break;
         PosIn P;
         const bool valid = fetch_position(kp.src, (int64_t)it * kp.src.stride, P);
@@ -268,17 +493,39 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) ld_kernel(KParams kp)
             L.m1 = rcp(1.0 + q);
             L.m2 = q * L.m1;
             L.y0 = {y1 - P.s * L.m1, P.y2};
+            L.rho = P.rho;
             status = 0;
             WorkCount tw;
-            // h at angle phi: a uniform disc of radius rho sin(phi)
-            auto eval = [&](double phi, double &h, double &e) {
+            // pieces: [0, cuts..., pi/2] in phi, cuts closer than 1e-9 merged
+            const int ncut = ld_cuts(L, P.rho, ed + 1);
+            int npc = 0;
+            if (lane == 0) {
+                ed[0] = 0.0;
+                int m = 0;
+                for (int k = 0; k < ncut; k++) {
+                    const double c = asin(fmin(ed[1 + k] / P.rho, 1.0));
+                    if (c - ed[m] > 1e-9 && halfpi - c > 1e-9) ed[++m] = c;
+                }
+                ed[++m] = halfpi;
+                npc = m;
+            }
+            npc = __shfl_sync(FULL, npc, 0);
+            __syncwarp();
+            // h at (piece, t): a uniform disc of radius rho sin(phi), times the
+            // substitution's factor; raw = mu(rho sin phi) sin^3 phi
+            auto eval = [&](int i, double t, double &h, double &e, double &raw) {
+                double jac;
+                const double phi = ld_map(ed, npc, i, t, jac);
+                h = e = raw = 0.0;
+                if (jac == 0.0 || phi == 0.0) return;
                 const double sn = sin(phi);
                 LensK Lr = L;
                 Lr.rho = P.rho * sn;
                 const PosResult r = integrate_position<PREC, 2, false, false, 1>(Lr, tol_u, kp.cap, ar, stage[wib], co);
                 const double w3 = sn * sn * sn * rcp(3.141592653589793238 * Lr.rho * Lr.rho);
-                h = w3 * r.area;
-                e = w3 * r.err;
+                raw = w3 * r.area;
+                h = jac * raw;
+                e = jac * w3 * r.err;
                 status |= r.status;
                 nsamp += r.nsamp;
                 tw.sw64 += r.work.sw64;
@@ -286,24 +533,35 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) ld_kernel(KParams kp)
                 tw.edges += r.work.edges;
                 tw.nw64 += r.work.nw64;
             };
-            // four panels of width pi/8: nodes j pi/32, j = 1..16
-            int np = 4;
-            if (lane == 0)
-                for (int p = 0; p < 4; p++) {
-                    pn[p * LD_PSTRIDE] = p * halfpi / 4;
-                    pn[p * LD_PSTRIDE + 1] = halfpi / 4;
-                    pe[2 * p] = 0.0;
-                }
-            if (lane == 0) pn[2] = 0.0;  // h(0) = 0
-            __syncwarp();
-            for (int j = 1; j <= 16; j++) {
-                double h, e;
-                eval(halfpi * j / 16, h, e);
-                if (lane == 0) {
-                    const int p = (j - 1) / 4, k = (j - 1) % 4 + 1;  // node k of panel p
-                    pn[p * LD_PSTRIDE + 2 + k] = h;
-                    pe[2 * p] += 0.25 * e;
-                    if (k == 4 && p + 1 < 4) pn[(p + 1) * LD_PSTRIDE + 2] = h;
+            // initial panels: one per piece, the rest (to four) to the widest pieces
+            int cnt[LD_MAXCUT + 1];
+            int np = 0;
+            for (int i = 0; i < npc; i++) cnt[i] = 1;
+            for (int k = npc; k < 4; k++) {
+                int bi = 0;
+                for (int i = 1; i < npc; i++)
+                    if ((ed[i + 1] - ed[i]) * cnt[bi] > (ed[bi + 1] - ed[bi]) * cnt[i]) bi = i;
+                cnt[bi]++;
+            }
+            double mrho = 0.0;
+            for (int i = 0; i < npc; i++) {
+                double hprev = 0.0;  // h at t = 0: sin^3(0) = 0, or tau' = 0 at a cut
+                for (int j = 0; j < cnt[i]; j++) {
+                    double hk[4], ek[4], raw = 0.0;
+                    for (int k = 1; k <= 4; k++)
+                        eval(i, (double)(4 * j + k) / (4 * cnt[i]), hk[k - 1], ek[k - 1], raw);
+                    if (lane == 0) {
+                        double *g = pn + np * LD_PSTRIDE;
+                        g[0] = i;
+                        g[1] = (double)j / cnt[i];
+                        g[2] = 1.0 / cnt[i];
+                        g[3] = hprev;
+                        for (int k = 0; k < 4; k++) g[4 + k] = hk[k];
+                        pe[2 * np] = 0.25 * (ek[0] + ek[1] + ek[2] + ek[3]);
+                    }
+                    hprev = hk[3];
+                    if (i == npc - 1 && j == cnt[i] - 1) mrho = raw;  // t = 1 of the last piece: phi = pi/2
+                    np++;
                 }
             }
             double T = 0.0, Eq = 0.0, Eu = 0.0;
@@ -316,7 +574,7 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) ld_kernel(KParams kp)
                     Eu = 0.0;
                     for (int p = 0; p < np; p++) {
                         const double *g = pn + p * LD_PSTRIDE;
-                        const double w = g[1], *h = g + 2;
+                        const double w = g[2], *h = g + 3;
                         const double s1 = w / 6.0 * (h[0] + 4.0 * h[2] + h[4]);
                         const double s2 = w / 12.0 * (h[0] + 4.0 * h[1] + 2.0 * h[2] + 4.0 * h[3] + h[4]);
                         const double e = fabs(s2 - s1) / 15.0;
@@ -331,34 +589,36 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) ld_kernel(KParams kp)
                             int pb = -1;
                             double eb = target / np;
                             for (int p = 0; p < np; p++)
-                                if (pe[2 * p + 1] > eb && pn[p * LD_PSTRIDE + 1] > halfpi * 1e-6) {
+                                if (pe[2 * p + 1] > eb && pn[p * LD_PSTRIDE + 2] > 1e-6) {
                                     eb = pe[2 * p + 1];
                                     pb = p;
                                 }
                             if (pb < 0) break;
                             pe[2 * pb + 1] = -1.0;  // taken
-                            const double a = pn[pb * LD_PSTRIDE], w = pn[pb * LD_PSTRIDE + 1];
+                            const double t0 = pn[pb * LD_PSTRIDE + 1], w = pn[pb * LD_PSTRIDE + 2];
                             // the four new nodes of its halves, and which panel they split
-                            for (int k = 0; k < 4; k++) sp[8 * nsplit + 2 * k] = a + w * (2 * k + 1) / 8.0;
+                            for (int k = 0; k < 4; k++) sp[8 * nsplit + 2 * k] = t0 + w * (2 * k + 1) / 8.0;
                             sp[8 * nsplit + 1] = (double)pb;
                             nsplit++;
                         }
+                        if (nsplit == 0) status |= PS_CAP;  // panel budget spent above the target
                     }
                 }
                 nsplit = __shfl_sync(FULL, nsplit, 0);
                 __syncwarp();
                 if (nsplit == 0) break;
                 for (int j = 0; j < nsplit; j++) {
-                    double hn[4], en[4];
-                    for (int k = 0; k < 4; k++) eval(sp[8 * j + 2 * k], hn[k], en[k]);
+                    const int pb = (int)sp[8 * j + 1];
+                    const int piece = (int)pn[pb * LD_PSTRIDE];
+                    double hn[4], en[4], raw;
+                    for (int k = 0; k < 4; k++) eval(piece, sp[8 * j + 2 * k], hn[k], en[k], raw);
                     if (lane == 0) {  // panel pb -> its left half in place, its right half appended
-                        const int pb = (int)sp[8 * j + 1];
                         double *g = pn + pb * LD_PSTRIDE, *r = pn + np * LD_PSTRIDE;
-                        const double a = g[0], w = g[1], h0 = g[2], h1 = g[3], h2 = g[4], h3 = g[5], h4 = g[6];
-                        r[0] = a + 0.5 * w; r[1] = 0.5 * w;
-                        r[2] = h2; r[3] = hn[2]; r[4] = h3; r[5] = hn[3]; r[6] = h4;
-                        g[1] = 0.5 * w;
-                        g[2] = h0; g[3] = hn[0]; g[4] = h1; g[5] = hn[1]; g[6] = h2;
+                        const double t0 = g[1], w = g[2], h0 = g[3], h1 = g[4], h2 = g[5], h3 = g[6], h4 = g[7];
+                        r[0] = piece; r[1] = t0 + 0.5 * w; r[2] = 0.5 * w;
+                        r[3] = h2; r[4] = hn[2]; r[5] = h3; r[6] = hn[3]; r[7] = h4;
+                        g[2] = 0.5 * w;
+                        g[3] = h0; g[4] = hn[0]; g[5] = h1; g[6] = hn[1]; g[7] = h2;
                         const double eo = pe[2 * pb];
                         pe[2 * pb] = 0.5 * eo + 0.25 * (en[0] + en[1]);
                         pe[2 * np] = 0.5 * eo + 0.25 * (en[2] + en[3]);
@@ -370,12 +630,8 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) ld_kernel(KParams kp)
             T = __shfl_sync(FULL, T, 0);
             Eq = __shfl_sync(FULL, Eq, 0);
             Eu = __shfl_sync(FULL, Eu, 0);
-            // mu(rho): the node at pi/2, the last node of the panel that ends there
-            double mrho = 0.0;
-            if (lane == 0)
-                for (int p = 0; p < np; p++)
-                    if (fabs(pn[p * LD_PSTRIDE] + pn[p * LD_PSTRIDE + 1] - halfpi) < 1e-12) mrho = pn[p * LD_PSTRIDE + 6];
             mrho = __shfl_sync(FULL, mrho, 0);
+            status = __shfl_sync(FULL, status, 0);
             const double inv = 1.0 / (1.0 - u / 3.0);
             mu = ((1.0 - u) * mrho + u * T) * inv;
             err = ((1.0 - u) * tol_u * mrho + u * (Eu + Eq)) * inv;
