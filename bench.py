@@ -108,7 +108,7 @@ def workload(name):
         return dict(kind="mag", name="stress_resonant_1e6", s=c["s"], q=c["q"], rho=c["rho"], y1=y1, y2=y2,
                     rel_tol=c["rel_tol"], n=y1.size)
     if name == "surrogate":
-        return dict(kind="surrogate", name="surrogate_fallback_1e7", n=10_000_000, ntrain=10_000_000, epochs=4,
+        return dict(kind="surrogate", name="surrogate_fallback_1e7", n=10_000_000, ntrain=10_000_000, epochs=30,
                     seed_train=0, seed_query=1, rel_tol=1e-4, kappa=3.0)
     if name == "batch_lightcurves":
         params, offsets, times = W.batch_lightcurves()
@@ -240,12 +240,18 @@ def golden_errors(wl, prec, P, wpath=None):
     from paper_2501_03322_gb300 import workloads as W
 
     err_est = None
+    extra = {}
     if wl["kind"] == "surrogate":
-        a = np.array([[float(v) for v in r[:7]] for r in golden_rows("surrogate_queries.txt")])
-        ok = a[:, 6] == 0
-        got, _ = P.surrogate_mag(wpath, *[a[ok, k].copy() for k in range(5)], rel_tol=wl["rel_tol"],
-                                 kappa=wl["kappa"], precision=prec)
-        ref, name = a[ok, 5], "surrogate_queries.txt"
+        a = np.array([[float(v) for v in r[:7]] for r in golden_rows("surrogate_queries.txt") +
+                      golden_rows("surrogate_band.txt")])
+        a = a[a[:, 6] == 0]
+        stat = np.zeros(len(a), np.int8)
+        got, _ = P.surrogate_mag(wpath, *[a[:, k].copy() for k in range(5)], rel_tol=wl["rel_tol"],
+                                 kappa=wl["kappa"], precision=prec, status=stat)
+        ref, name = a[:, 5], "surrogate_queries.txt+surrogate_band.txt"
+        net = stat == P.POS_NETWORK
+        if net.any():
+            extra = {"network_answered": int(net.sum()), "network_max_rel_err": float(np.abs(got[net] / ref[net] - 1).max())}
     elif wl["kind"] == "multi":
         name = "fig6_sweep.txt"
         a = np.array([[float(v) for v in r[1:8]] for r in golden_rows(name)])
@@ -289,7 +295,7 @@ def golden_errors(wl, prec, P, wpath=None):
                                                 details=True)
     rel = np.abs(np.asarray(got) / ref - 1.0)
     out = {"golden": name, "positions": int(rel.size), "max_rel_err": float(rel.max()),
-           "p999_rel_err": float(np.quantile(rel, 0.999)), "rel_tol": wl["rel_tol"]}
+           "p999_rel_err": float(np.quantile(rel, 0.999)), "rel_tol": wl["rel_tol"], **extra}
     if err_est is not None:
         out["estimate_bounds_error"] = float(np.mean(np.abs(np.asarray(got) - ref) <= np.asarray(err_est)
                                                      + 1e-12 * ref))
@@ -547,7 +553,7 @@ def main():
             P.lightcurve_batch(pd, od, td, rel_tol=wl["rel_tol"], out=outd, **kw)
     else:
         wpath = os.path.join(ROOT, "paper_2501_03322_gb300", "_build",
-                             "surrogate_s%d_n%d_e%d.bin" % (wl["seed_train"], wl["ntrain"], wl["epochs"]))
+                             "surrogate_v2_s%d_n%d_e%d.bin" % (wl["seed_train"], wl["ntrain"], wl["epochs"]))
         t0 = time.perf_counter()
         if rank == 0 and not os.path.exists(wpath):  # one training run; the other ranks read its weights
             wl["train_stats"] = P.surrogate_train(wpath, wl["ntrain"], wl["seed_train"], wl["epochs"])

@@ -72,12 +72,15 @@ enum {
                               images and parity sum -1 (Sec. 2.3) */
     TW_POS_NONFINITE = 4,  /* non-finite input position or result (out is NaN) */
     TW_POS_SOLVER = 8,     /* root iteration stopped at its iteration limit */
-    TW_POS_SLOPE = 16      /* a caustic crossing failed the slope test
+    TW_POS_SLOPE = 16,     /* a caustic crossing failed the slope test
                               (Sec. 2.4.2): its pair of merging images was
                               not perpendicular to the ghost pair across it;
                               the crossing was moved to the slope jump, or a
                               false image piece removed, where the walk along
                               the five-image run found one */
+    TW_POS_EXPANSION = 32, /* tw_surrogate_mag: answered by the point-source
+                              expansion (no contour integration) */
+    TW_POS_NETWORK = 64    /* tw_surrogate_mag: answered by the network */
 };
 
 /* Arithmetic modes. */
@@ -209,43 +212,64 @@ int tw_mag_noalloc(double s, double q, double rho, const double *y1, const doubl
                    double rel_tol, double *out, int precision, int max_samples, void *stream);
 
 /* MLP surrogate (not in the paper; a systems pattern of this library).  A
- * BF16 network 5 -> 256 -> 256 -> 256 -> 256 -> 2 maps (log10 s, log10 q,
- * log10 rho, y1, y2) to r = ln(mu / A_hex) and l = ln(sigma), A_hex being the
- * hexadecapole approximation of the finite-source magnification from
- * point-source magnifications (images of Eq. 6, Jacobian of Eq. 7) at the
- * source centre and at 8 points on rings of radius rho/2, rho and 2 rho; the hidden
- * layers run on the tensor cores.
+ * BF16 network 8 -> 256 -> 256 -> 256 -> 256 -> 2 maps (log10 s, log10 q,
+ * log10 rho, y1, y2) and three features of the point-source expansion of the
+ * same query to (r, l).  The expansion is the hexadecapole approximation
+ * A_hex of the finite-source magnification from point-source magnifications
+ * (images of Eq. 6, Jacobian of Eq. 7) at the source centre and at 8 points
+ * on rings of radius rho/2, rho and 2 rho; its features are the decade of its
+ * error estimate, the signed gap between its (rho/2, rho) and (rho, 2 rho)
+ * values in units of that estimate, and the signed size of the finite-source
+ * correction.  The network predicts mu = A_hex (1 + gap / 15) exp(r) (the
+ * factor is the Richardson step between the two ring pairs) with
+ * uncertainty sigma = exp(l) in ln mu; the hidden layers run on the tensor
+ * cores.
  *
  * tw_surrogate_train draws nsamples positions near caustics (a random point of
  * a random branch of the caustic of a random lens with log10 s ~ U[-0.5, 0.5],
  * log10 q ~ U[-5, -1], log10 rho ~ U[-4, -2], displaced uniformly within three
- * times that branch's size) from `seed`, labels those that are not flagged as
- * near a caustic with the contour integrator (FP64, rel_tol 1e-5), trains for
- * `epochs` epochs (Gaussian likelihood, Adam, batch 4096) and writes the
- * weights file (magic, shapes, standardisation, FP32 weights, checksum).
- * stats (optional, [5]): positions drawn, positions labelled, training rows,
- * mean loss of the last epoch, spread of the targets.  Synchronous. */
+ * times that branch's size) from `seed`.  The network's band is the positions
+ * not flagged as near a caustic (see tw_surrogate_mag) whose expansion error
+ * estimate lies in (2.5e-5, 2e-3]: below half of a 1e-4 tolerance the
+ * expansion answers by itself, and the bound keeps the correction the
+ * network adds small.  Those are labelled by contour integration (FP64,
+ * rel_tol 1e-6) in draw order; the last tenth is held out, the rest (a
+ * multiple of 4096) trains for `epochs` epochs (Gaussian likelihood of the
+ * standardised r, Adam, batch 4096, cosine learning rate).  The held-out rows
+ * calibrate kappa_cal: the 99.9% quantile of |r - r_net| / sigma (at least
+ * 3), raised until every held-out row it would answer at rel_tol 1e-4 is
+ * within 2.5e-5.  The weights file holds magic, shapes, the standardisation record
+ * (inputs, target, kappa_cal, band), FP32 weights and a checksum.  stats
+ * (optional, [9]): positions drawn, positions in the band, training rows,
+ * mean loss of the last epoch, spread of the targets, held-out rows,
+ * kappa_cal, the fraction of held-out rows the network would answer at
+ * rel_tol 1e-4 and the largest error in ln mu among them.  TW_EINVAL if the
+ * band holds fewer than 4096 training or 128 held-out rows.  Synchronous. */
 int tw_surrogate_train(const char *weights_path, int64_t nsamples, uint64_t seed, int epochs, double *stats,
                        const tw_opts *opts);
 
 /* Surrogate magnification of n queries with per-query lens and source radius
- * (arrays s, q, rho, y1, y2; host or device, all of one kind).  A query that
- * is not flagged as near a caustic (the caustic, swept at 64 angles, comes
- * within 4 rho of the centre; the image count differs between the centre and
- * a ring point; min |J| < 0.1 at the centre; or the expansion's error
- * estimate exceeds 5% of the value) is answered without contour integration
- * when its predicted error is within rel_tol: the expansion's error estimate
+ * (arrays s, q, rho, y1, y2; host or device, all of one kind).  A query is
+ * flagged as near a caustic when the caustic, swept at 64 angles, comes
+ * within 4 rho of the centre, the image count differs between the centre and
+ * a ring point, min |J| < 0.1 at the centre, or the expansion's error
+ * estimate exceeds 5% of the value.  An unflagged query is answered without
+ * contour integration by the expansion (mu = A_hex) when its error estimate
  * (the gap between its values from the rings (rho/2, rho) and (rho, 2 rho),
  * floored at a twentieth of the finite-source correction |A_hex - A_0|) is
- * below 0.5 rel_tol (mu = A_hex), or the network's
- * kappa * sigma <= rel_tol (mu = A_hex exp(r)).  All other queries fall back
- * to contour integration (one persistent launch over them, with
- * opts->precision and opts->max_samples).  out[i] receives mu; counts
- * (optional, [5]) the number of fallbacks, of queries accepted by the
- * network, of queries accepted by the expansion, and the fallbacks split
+ * below 0.5 rel_tol, else by the network when the estimate lies in the
+ * network's band (2.5e-5, 2e-3] and max(kappa, kappa_cal) * sigma <=
+ * rel_tol.  All other
+ * queries fall back to contour integration (one persistent launch over them,
+ * with opts->precision and opts->max_samples).  out[i] receives mu; counts
+ * (optional, [5]) the number of fallbacks, of queries answered by the
+ * network, of queries answered by the expansion, and the fallbacks split
  * into those flagged as near a caustic and the unflagged ones that neither
- * the expansion nor the network certified.  n < 2^31.  Synchronous.  The
- * library keeps the call's device buffers for the next call on the device. */
+ * the expansion nor the network answered.  opts->pos_status (optional, [n],
+ * the kind of the other arrays) receives TW_POS_EXPANSION or TW_POS_NETWORK
+ * for answered queries and the contour status bits for fallbacks.  n < 2^31.
+ * Synchronous.  The library keeps the call's device buffers for the next
+ * call on the device. */
 int tw_surrogate_mag(const char *weights_path, const double *s, const double *q, const double *rho,
                      const double *y1, const double *y2, int64_t n, double rel_tol, double kappa, double *out,
                      int64_t *counts, const tw_opts *opts);

@@ -27,6 +27,7 @@ from . import build as _build
 
 TW_OK, TW_EINVAL, TW_ECUDA, TW_ENOMEM, TW_ETIMEOUT, TW_ETOOBIG, TW_WCAP = 0, -1, -2, -3, -4, -5, 1
 POS_CAP, POS_IMAGECOUNT, POS_NONFINITE, POS_SOLVER, POS_SLOPE = 1, 2, 4, 8, 16
+POS_EXPANSION, POS_NETWORK = 32, 64  # tw_surrogate_mag: answered without contour integration
 PREC_FP64, PREC_MIXED = 0, 1
 
 _lock = threading.Lock()
@@ -227,11 +228,13 @@ def gemm_bf16(A, B, out=None, stream=None):
 
 def surrogate_train(path, nsamples=1_000_000, seed=0, epochs=4, stream=None):
     """Train the MLP surrogate (tw_surrogate_train); returns its statistics."""
-    st = np.zeros(5)
+    st = np.zeros(9)
     o = make_opts(stream=getattr(stream, "cuda_stream", stream))
     _check(lib().tw_surrogate_train(str(path).encode(), int(nsamples), int(seed), int(epochs),
                                     st.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o)))
-    return dict(drawn=int(st[0]), labelled=int(st[1]), rows=int(st[2]), loss=float(st[3]), target_std=float(st[4]))
+    return dict(drawn=int(st[0]), labelled=int(st[1]), rows=int(st[2]), loss=float(st[3]), target_std=float(st[4]),
+                heldout=int(st[5]), kappa_cal=float(st[6]), heldout_accepted=float(st[7]),
+                heldout_accepted_max_err=float(st[8]))
 
 
 def surrogate_sample(seed, n, device="cuda"):
@@ -245,17 +248,20 @@ def surrogate_sample(seed, n, device="cuda"):
 
 
 def surrogate_mag(path, s, q, rho, y1, y2, rel_tol=1e-4, kappa=3.0, precision=PREC_FP64, max_samples=4096, out=None,
-                  stream=None, details=False):
+                  stream=None, details=False, status=None):
     """Surrogate magnification with contour fallback (tw_surrogate_mag).
 
     Returns (out, n_fallback) or, with details=True, (out, counts) where counts =
-    dict(fallback=..., network=..., expansion=...)."""
+    dict(fallback=..., network=..., expansion=...).  `status` (optional int8
+    array of the inputs' kind) receives POS_EXPANSION / POS_NETWORK for the
+    queries answered without contour integration, contour status bits for the
+    others."""
     arrs = [_prep(a) for a in (s, q, rho, y1, y2)]
     n = int(arrs[0].shape[0])
     if out is None:
         out = _alloc_like(arrs[0], n, np.float64, "float64")
     c = np.zeros(5, np.int64)
-    o = make_opts(precision, 64, max_samples, _stream_of(arrs[0], stream))
+    o = make_opts(precision, 64, max_samples, _stream_of(arrs[0], stream), status=status)
     _check(lib().tw_surrogate_mag(str(path).encode(), *[_ptr(a) for a in arrs], n, rel_tol, kappa, _ptr(out),
                                   c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o)))
     if details:

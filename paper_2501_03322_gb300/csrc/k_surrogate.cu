@@ -1,16 +1,18 @@
 // k_surrogate.cu -- BF16 MLP surrogate of the finite-source magnification,
 // with contour-integration fallback; training and inference.
 //
-// The network maps x = (log10 s, log10 q, log10 rho, y1, y2) (standardised)
-// through 5 -> 256 -> 256 -> 256 -> 256 -> 2 (ReLU) to (r, l): r is the
-// logarithm of the ratio of the finite-source magnification to its
+// The network maps x = (log10 s, log10 q, log10 rho, y1, y2, and three
+// features of the query's point-source expansion; standardised) through
+// 8 -> 256 -> 256 -> 256 -> 256 -> 2 (ReLU) to (r, l).  The expansion is the
 // hexadecapole approximation A_hex (point-source magnifications at the centre
 // and on rings, Gould 2008; the paper tests point-source adequacy the same
-// way, Sec. 2.3), l = ln(sigma) its predicted uncertainty, so mu = A_hex exp(r).
-// Learning only what the expansion misses keeps the BF16 network's errors on
-// a quantity that is tiny away from caustics.  The three 256 x 256 layers run on the
-// tensor cores (k_gemm.cu, BF16 weights and activations, FP32 accumulation);
-// the 5 -> 256 input layer and the 256 -> 2 head run in FP32 on CUDA cores.
+// way, Sec. 2.3); the network predicts mu = A_hex (1 + gap / 15) exp(r), the
+// middle factor being the Richardson step between the expansions from two
+// ring pairs, and l = ln(sigma) its uncertainty in ln mu.  Learning only what
+// the expansion misses keeps the BF16 network's errors on a quantity that is
+// tiny away from caustics.  The three 256 x 256 layers run on the tensor
+// cores (k_gemm.cu, BF16 weights and activations, FP32 accumulation); the
+// input layer and the 256 -> 2 head run in FP32 on CUDA cores.
 //
 // Inference: per query, point-source images (Eq. 6 quintic, FP32 Aberth +
 // FP64 Newton, residual ghost test, A = sum 1/|J|) at the centre and at 8
@@ -18,24 +20,28 @@
 // approximation with its error estimate, a near-caustic flag (the image count
 // differs between the centre and a ring point, min |J| < 0.1 at the centre, or
 // the error estimate exceeds 5% of the value), the MLP, and the fallback
-// decision: flagged, or neither the expansion's error estimate nor
-// kappa * sigma is within rel_tol.  The flag also sweeps the
-// caustic itself: a caustic smaller than the ring spacing can sit inside the
-// source without any ring point seeing it.  Fallback
-// queries are integrated by the contour kernel in one persistent launch.
+// decision: flagged, or neither the expansion's error estimate nor the
+// network's calibrated kappa * sigma is within rel_tol.  The flag also sweeps
+// the caustic itself: a caustic smaller than the ring spacing can sit inside
+// the source without any ring point seeing it.  Fallback queries are
+// integrated by the contour kernel in one persistent launch.
 //
 // Training: positions are drawn near caustics (a random point of a random
 // branch of the caustic, displaced uniformly in a disc of three times that
-// branch's bounding-box size), labelled by the contour integrator (FP64 mode),
-// and the network is fitted by the Gaussian negative log-likelihood of r with
-// Adam on FP32 master weights.  Flagged (near-caustic) samples are left out of
-// training: they always fall back.
+// branch's bounding-box size).  The network is trained only where it can
+// answer: unflagged positions whose expansion error estimate is above a
+// quarter of 1e-4 (below half the tolerance the expansion answers by
+// itself) and at most 2e-3.  These are labelled by the contour integrator (FP64, rel_tol
+// 1e-6), and the network is fitted by the Gaussian negative log-likelihood of
+// the standardised r with Adam on FP32 master weights; a held-out tenth
+// calibrates the acceptance factor kappa.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -48,8 +54,8 @@
 namespace tw {
 
 constexpr int SH = 256;   // hidden width
-constexpr int SNIN = 5;   // inputs
-constexpr int SXP = 8;    // padded input row (floats)
+constexpr int SNIN = 8;   // inputs: the five query parameters and three expansion features
+constexpr int SXP = 8;    // input row (floats)
 // offsets in the FP32 parameter blob (weights stored [out][in])
 constexpr int OW1 = 0, OB1 = OW1 + SH * SNIN;
 constexpr int OW2 = OB1 + SH, OB2 = OW2 + SH * SH;
@@ -60,8 +66,14 @@ constexpr int NPAR = OB5 + 2;
 constexpr int OWH[3] = {OW2, OW3, OW4};
 constexpr int OBH[3] = {OB2, OB3, OB4};
 
+// Input standardisation, target standardisation (the network's r is
+// tmean + tstd * a, its sigma tstd * exp(b)), the acceptance factor
+// calibrated on held-out rows, and the expansion-error band the network was
+// trained on (it answers only queries whose expansion error estimate lies in
+// (band, band_hi]).
 struct SurNorm {
     float mean[SNIN], inv_std[SNIN];
+    float tmean, tstd, kappa_cal, band, band_hi;
 };
 
 // ------------------------------------------------------------ random numbers
@@ -448,7 +460,7 @@ __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const d
         }
     }
     __syncwarp();
-    double Ahex = A0, hexe = 1.0;
+    double Ahex = A0, hexe = 1.0, dgap = 0.0, corr = 0.0;
     if (want) {
         double R[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -469,7 +481,9 @@ __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const d
             // to 25x on about 1e-5 of the queries, all with corrections of
             // 0.2-6%; the floor limits the expansion to corrections of at most
             // 10 rel_tol.
-            hexe = fmax(fabs(disc(R[1], R[2], 1.0) - Ahex), 0.05 * fabs(Ahex - A0)) / Ahex;
+            dgap = (disc(R[1], R[2], 1.0) - Ahex) / Ahex;
+            corr = (Ahex - A0) / Ahex;
+            hexe = fmax(fabs(dgap), 0.05 * fabs(corr));
             // a series that is not converging marks the neighbourhood of a caustic
             if (!(Ahex > 0.0) || !(hexe <= 0.05)) flag = true;
         }
@@ -478,6 +492,16 @@ __global__ void __launch_bounds__(128, 3) sur_features_kernel(int64_t n, const d
         MUPS[i] = ok ? Ahex : __longlong_as_double(0x7ff8000000000000ll);
         FLAG[i] = flag ? 1 : 0;
         HEXE[i] = (float)fmin(hexe, 1.0);
+        // expansion features of the network: the decade of the error estimate,
+        // the signed ring gap in units of it (the gap over 15 is the
+        // Richardson step from the (rho/2, rho) expansion towards the exact
+        // disc average, the c3 rho^6 term above) and the signed size of the
+        // finite-source correction
+        float *x = X + i * SXP;
+        const bool fin = !flag && hexe > 0.0;
+        x[5] = fin ? (float)log10(fmax(hexe, 1e-10)) : 0.f;
+        x[6] = fin ? (float)(dgap / hexe) : 0.f;
+        x[7] = fin ? (float)copysign(log10(1.0 + 1e6 * fabs(corr)), corr) : 0.f;
     }
     if (WORK) {
         const int a = __reduce_add_sync(0xffffffffu, w_solve), b = __reduce_add_sync(0xffffffffu, w_sweep);
@@ -509,10 +533,22 @@ __global__ void sur_layer1_kernel(int64_t rows, const float *X, const float *P, 
     if (XS && o < SXP) XS[r * SXP + o] = o < SNIN ? xs[o] : 0.f;
 }
 
-// Head (256 -> 2) and fallback decision; one warp per query.
+// Richardson step of the expansion (ln of A_hex (1 + gap / 15)), the base
+// the network's r is added to; X holds the query's features.
+__device__ __forceinline__ double richardson_base(const float *x, float hexe) {
+    return log1p((double)x[6] * (double)hexe / 15.0);
+}
+
+// Head (256 -> 2) and fallback decision; one warp per query.  A query is
+// answered by the expansion when its error estimate is within half the
+// tolerance, else by the network when it lies in the network's band and
+// max(kappa, kappa_cal) sigma <= tol; every other query is queued for contour
+// integration.  PSTAT (optional) receives TW_POS_EXPANSION or TW_POS_NETWORK
+// for the answered queries.
 __global__ void sur_head_infer_kernel(int64_t n, int64_t row0, const __nv_bfloat16 *H4, const float *P,
-                                      const double *MUPS, const uint8_t *FLAG, const float *HEXE, double tol,
-                                      float kappa, double *OUT, int32_t *LIST, unsigned long long *NLIST) {
+                                      const float *X, SurNorm nrm, const double *MUPS, const uint8_t *FLAG,
+                                      const float *HEXE, double tol, float kappa, double *OUT, int8_t *PSTAT,
+                                      int32_t *LIST, unsigned long long *NLIST) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n) return;
@@ -532,12 +568,12 @@ __global__ void sur_head_infer_kernel(int64_t n, int64_t row0, const __nv_bfloat
     }
     if (lane == 0) {
         const int64_t g = row0 + w;
-        const float r = a + P[OB5], l = b + P[OB5 + 1];
-        // accepted by the expansion itself when its error estimate is within
-        // half the tolerance, else by the network when kappa sigma <= tol
-        const bool hex_ok = HEXE[g] <= 0.5f * (float)tol;
-        const bool mlp_ok = kappa * expf(l) <= (float)tol;
-        const double mu = hex_ok ? MUPS[g] : MUPS[g] * exp((double)r);
+        const float hx = HEXE[g];
+        const double r = (double)nrm.tmean + (double)nrm.tstd * (double)(a + P[OB5]);
+        const float sig = nrm.tstd * expf(fminf(fmaxf(b + P[OB5 + 1], -25.f), 5.f));
+        const bool hex_ok = hx <= 0.5f * (float)tol;
+        const bool mlp_ok = hx > nrm.band && hx <= nrm.band_hi && fmaxf(kappa, nrm.kappa_cal) * sig <= (float)tol;
+        const double mu = hex_ok ? MUPS[g] : MUPS[g] * exp(richardson_base(X + w * SXP, hx) + r);
         if (FLAG[g] || !(hex_ok || mlp_ok) || !isfinite(mu)) {
             const unsigned long long slot = atomicAdd(NLIST, 1ull);
             LIST[slot] = (int32_t)g;
@@ -545,6 +581,7 @@ __global__ void sur_head_infer_kernel(int64_t n, int64_t row0, const __nv_bfloat
             if (FLAG[g]) atomicAdd(NLIST + 3, 1ull);
         } else {
             OUT[g] = mu;
+            if (PSTAT) PSTAT[g] = (int8_t)(hex_ok ? TW_POS_EXPANSION : TW_POS_NETWORK);
             atomicAdd(NLIST + (hex_ok ? 2 : 1), 1ull);
         }
     }
@@ -643,7 +680,9 @@ __global__ void colsum_bf16_kernel(int B, const __nv_bfloat16 *Gm, float *out) {
 __global__ void sur_layer1_bwd_kernel(int B, const float *DH1, const __nv_bfloat16 *H1, const float *XS, float *G) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= SH) return;
-    float gw[SNIN] = {0.f, 0.f, 0.f, 0.f, 0.f}, gb = 0.f;
+    float gw[SNIN], gb = 0.f;
+#pragma unroll
+    for (int k = 0; k < SNIN; k++) gw[k] = 0.f;
     for (int b = 0; b < B; b++) {
         const float g = __bfloat162float(H1[(size_t)b * SH + o]) > 0.f ? DH1[(size_t)b * SH + o] : 0.f;
         gb += g;
@@ -677,21 +716,60 @@ __global__ void refresh_bf16_kernel(const float *Pm, __nv_bfloat16 *Wf, __nv_bfl
     Wt[(size_t)l * SH * SH + (size_t)k * SH + o] = v;
 }
 
-// Targets r = ln(mu) - ln(mu_ps) and weights (0 for flagged or non-finite).
-__global__ void sur_targets_kernel(int64_t n, const double *MU, const double *MUPS, const uint8_t *FLAG, float *T,
-                                   float *WT) {
+// Targets r = ln(mu) - ln(A_hex) - (Richardson base) and weights: 1 for the
+// rows of the network's band (not flagged, expansion error estimate in
+// (band, band_hi]) whose label converged, else 0.
+__global__ void sur_targets_kernel(int64_t n, const double *MU, const double *MUPS, const uint8_t *FLAG,
+                                   const float *HEXE, const float *X, const int8_t *LSTAT, float band, float band_hi,
+                                   float *T, float *WT) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double r = log(MU[i]) - log(MUPS[i]);
-    const bool ok = !FLAG[i] && isfinite(r);
+    const double r = log(MU[i]) - log(MUPS[i]) - richardson_base(X + i * SXP, HEXE[i]);
+    const bool ok = !FLAG[i] && HEXE[i] > band && HEXE[i] <= band_hi && LSTAT[i] == 0 && isfinite(r);
     T[i] = ok ? (float)r : 0.f;
     WT[i] = ok ? 1.f : 0.f;
 }
 
-__global__ void compact_unflagged_kernel(int64_t n, const uint8_t *FLAG, int32_t *LIST, unsigned long long *NLIST) {
+// indices of the rows in the network's band
+__global__ void compact_band_kernel(int64_t n, const uint8_t *FLAG, const float *HEXE, float band, float band_hi,
+                                    int32_t *LIST, unsigned long long *NLIST) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || FLAG[i]) return;
+    if (i >= n || FLAG[i] || !(HEXE[i] > band && HEXE[i] <= band_hi)) return;
     LIST[atomicAdd(NLIST, 1ull)] = (int32_t)i;
+}
+
+// (t - mean) / std in place
+__global__ void standardise_kernel(int64_t n, float *T, float mean, float inv_std) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) T[i] = (T[i] - mean) * inv_std;
+}
+
+// Held-out evaluation: per row the head's standardised error |t - a| / exp(b)
+// (Z) and its sigma in units of r (SIG).
+__global__ void sur_head_eval_kernel(int B, const __nv_bfloat16 *H4, const float *P, const float *T, float tstd,
+                                     float *Z, float *SIG) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= B) return;
+    const uint4 v = *(const uint4 *)(H4 + (size_t)w * SH + lane * 8);
+    const __nv_bfloat16 *h = (const __nv_bfloat16 *)&v;
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const float x = __bfloat162float(h[j]);
+        a = fmaf(P[OW5 + lane * 8 + j], x, a);
+        b = fmaf(P[OW5 + SH + lane * 8 + j], x, b);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        const float l = fminf(fmaxf(b + P[OB5 + 1], -25.f), 5.f);
+        Z[w] = fabsf(T[w] - (a + P[OB5])) * expf(-l);
+        SIG[w] = tstd * expf(l);
+    }
 }
 
 // rows of X, T, WT selected by LIST, into dense training arrays
@@ -741,12 +819,13 @@ static uint64_t fnv1a(const void *data, size_t n, uint64_t h = 14695981039346656
 
 static const char MAGIC[8] = {'T', 'W', 'M', 'L', 'P', '0', '0', '1'};
 
-// Weights file: magic, int32 {version 1, hidden, inputs, nparams}, the
-// standardisation (mean, 1/std), the FP32 parameters, FNV-1a checksum.
+// Weights file: magic, int32 {version 2, hidden, inputs, nparams}, the
+// standardisation record (input mean and 1/std, target mean and spread,
+// calibrated kappa, band), the FP32 parameters, FNV-1a checksum.
 static int save_model(const char *path, const std::vector<float> &P, const SurNorm &nrm) {
     FILE *f = fopen(path, "wb");
     if (!f) return TW_EINVAL;
-    const int32_t hdr[4] = {1, SH, SNIN, NPAR};
+    const int32_t hdr[4] = {2, SH, SNIN, NPAR};
     uint64_t h = fnv1a(MAGIC, 8);
     h = fnv1a(hdr, sizeof(hdr), h);
     h = fnv1a(&nrm, sizeof(nrm), h);
@@ -765,7 +844,7 @@ static int load_model(const char *path, std::vector<float> &P, SurNorm &nrm) {
     uint64_t h = 0;
     P.assign(NPAR, 0.f);
     bool ok = fread(mg, 8, 1, f) == 1 && memcmp(mg, MAGIC, 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
-              hdr[0] == 1 && hdr[1] == SH && hdr[2] == SNIN && hdr[3] == NPAR &&
+              hdr[0] == 2 && hdr[1] == SH && hdr[2] == SNIN && hdr[3] == NPAR &&
               fread(&nrm, sizeof(nrm), 1, f) == 1 && fread(P.data(), 4, NPAR, f) == (size_t)NPAR &&
               fread(&h, 8, 1, f) == 1;
     fclose(f);
@@ -908,49 +987,76 @@ extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, ui
         (rc = B.get(&T, n)) || (rc = B.get(&WT, n)) || (rc = B.get(&FLAG, n)) || (rc = B.get(&LIST, n)) ||
         (rc = B.get(&NL, 1)) || (rc = B.get(&err, 1)))
         return rc;
-    // positions near caustics, point-source values and flags, contour labels
+    // positions near caustics, point-source values and flags
     sur_sample_kernel<<<nblk(n, 128), 128, 0, st>>>(seed, n, S, Q, RHO, Y1, Y2);
     float *HEXE;
-    if ((rc = B.get(&HEXE, n))) return rc;
+    int8_t *LSTAT;
+    if ((rc = B.get(&HEXE, n)) || (rc = B.get(&LSTAT, n))) return rc;
     sur_features_kernel<<<nblk(n, 128), 128, 0, st>>>(n, S, Q, RHO, Y1, Y2, X, MUPS, FLAG, HEXE, nullptr);
     cudaMemsetAsync(NL, 0, 8, st);
     cudaMemsetAsync(err, 0, 4, st);
-    compact_unflagged_kernel<<<nblk(n, 256), 256, 0, st>>>(n, FLAG, LIST, NL);
+    cudaMemsetAsync(LSTAT, 0x7f, n, st);
+    // the network's band: unflagged positions whose expansion error estimate
+    // is above a quarter of 1e-4 (below half the tolerance the expansion
+    // answers by itself) and at most 2e-3, so that the correction the network
+    // adds is small (at most about twenty times the 1e-4 target); in draw
+    // order, so that training is reproducible
+    const float band = 2.5e-5f, band_hi = 2e-3f;
+    compact_band_kernel<<<nblk(n, 256), 256, 0, st>>>(n, FLAG, HEXE, band, band_hi, LIST, NL);
     unsigned long long nl = 0;
     cudaError_t e = cudaMemcpyAsync(&nl, NL, 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cerr(e);
-    if (nl < 4096) return TW_EINVAL;  // not enough trainable samples
-    // labels one decade tighter than the 1e-4 target, in FP64 mode
-    rc = contour_positions(S, Q, RHO, Y1, Y2, LIST, (int64_t)nl, 1e-5, TW_PREC_FP64, 4096, MU, nullptr, st);
-    if (rc) return rc;
-    sur_targets_kernel<<<nblk(n, 256), 256, 0, st>>>(n, MU, MUPS, FLAG, T, WT);
-    // dense training set of the unflagged samples
     const int BATCH = 4096;
-    const int64_t m = ((int64_t)nl / BATCH) * BATCH;
+    const int64_t nho = (int64_t)nl / 10;                        // held-out rows (calibration)
+    const int64_t m = (((int64_t)nl - nho) / BATCH) * BATCH;     // training rows
+    if (m < BATCH || nho < 128) return TW_EINVAL;                // not enough positions in the band
+    {
+        std::vector<int32_t> hl(nl);
+        e = cudaMemcpyAsync(hl.data(), LIST, nl * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cerr(e);
+        std::sort(hl.begin(), hl.end());
+        e = cudaMemcpyAsync(LIST, hl.data(), nl * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cerr(e);
+    }
+    // labels two decades tighter than the 1e-4 target, FP64 contour integration
+    rc = contour_positions(S, Q, RHO, Y1, Y2, LIST, (int64_t)nl, 1e-6, TW_PREC_FP64, 4096, MU, LSTAT, st);
+    if (rc) return rc;
+    sur_targets_kernel<<<nblk(n, 256), 256, 0, st>>>(n, MU, MUPS, FLAG, HEXE, X, LSTAT, band, band_hi, T, WT);
+    // dense rows of the band: the first m train, the last nho calibrate
+    const int64_t nrow = m + nho, nho_pad = ((nho + 127) / 128) * 128;
     float *Xc, *Tc, *WTc;
-    if ((rc = B.get(&Xc, m * SXP)) || (rc = B.get(&Tc, m)) || (rc = B.get(&WTc, m))) return rc;
-    gather_train_kernel<<<nblk(m, 256), 256, 0, st>>>(m, LIST, X, T, WT, Xc, Tc, WTc);
-    // standardisation from up to 65536 training rows
-    const int64_t ns = m < 65536 ? m : 65536;
-    std::vector<float> hx(ns * SXP), ht(ns), hw(ns);
-    e = cudaMemcpyAsync(hx.data(), Xc, ns * SXP * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ht.data(), Tc, ns * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hw.data(), WTc, ns * 4, cudaMemcpyDeviceToHost, st);
+    if ((rc = B.get(&Xc, (m + nho_pad) * SXP)) || (rc = B.get(&Tc, m + nho_pad)) || (rc = B.get(&WTc, m + nho_pad)))
+        return rc;
+    cudaMemsetAsync(Xc, 0, (m + nho_pad) * SXP * 4, st);
+    gather_train_kernel<<<nblk(nrow, 256), 256, 0, st>>>(nrow, LIST + ((int64_t)nl - nrow), X, T, WT, Xc, Tc, WTc);
+    // input and target standardisation from the training rows
+    std::vector<float> hx(m * SXP), ht(m), hw(m);
+    e = cudaMemcpyAsync(hx.data(), Xc, m * SXP * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ht.data(), Tc, m * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hw.data(), WTc, m * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cerr(e);
     SurNorm nrm;
     double tsum = 0, tsq = 0, wsum = 0;
     for (int k = 0; k < SNIN; k++) {
         double a = 0, b = 0;
-        for (int64_t i = 0; i < ns; i++) { a += hx[i * SXP + k]; b += (double)hx[i * SXP + k] * hx[i * SXP + k]; }
-        a /= ns;
-        b = b / ns - a * a;
+        for (int64_t i = 0; i < m; i++) { a += hx[i * SXP + k]; b += (double)hx[i * SXP + k] * hx[i * SXP + k]; }
+        a /= m;
+        b = b / m - a * a;
         nrm.mean[k] = (float)a;
         nrm.inv_std[k] = (float)(1.0 / sqrt(b > 1e-20 ? b : 1e-20));
     }
-    for (int64_t i = 0; i < ns; i++) { tsum += hw[i] * ht[i]; tsq += hw[i] * ht[i] * ht[i]; wsum += hw[i]; }
-    const double tmean = tsum / (wsum > 0 ? wsum : 1), tstd = sqrt(fmax(tsq / (wsum > 0 ? wsum : 1) - tmean * tmean, 1e-20));
+    for (int64_t i = 0; i < m; i++) { tsum += hw[i] * ht[i]; tsq += (double)hw[i] * ht[i] * ht[i]; wsum += hw[i]; }
+    const double tmean = tsum / (wsum > 0 ? wsum : 1), tstd = sqrt(fmax(tsq / (wsum > 0 ? wsum : 1) - tmean * tmean, 1e-24));
+    nrm.tmean = (float)tmean;
+    nrm.tstd = (float)tstd;
+    nrm.kappa_cal = 3.f;
+    nrm.band = band;
+    nrm.band_hi = band_hi;
+    standardise_kernel<<<nblk(nrow, 256), 256, 0, st>>>(nrow, Tc, (float)tmean, (float)(1.0 / tstd));
     // initial weights (He-uniform, seeded), head bias at the target mean / spread
     std::vector<float> hP(NPAR, 0.f);
     uint64_t rs = seed ^ 0xA0761D6478BD642Full;
@@ -966,8 +1072,8 @@ extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, ui
     for (int l = 0; l < 3; l++)
         for (int i = 0; i < SH * SH; i++) hP[OWH[l] + i] = (float)((2 * urand() - 1) * sqrt(6.0 / SH));
     for (int i = 0; i < 2 * SH; i++) hP[OW5 + i] = (float)((2 * urand() - 1) * 1e-3);
-    hP[OB5] = (float)tmean;
-    hP[OB5 + 1] = (float)log(tstd);
+    hP[OB5] = 0.f;      // standardised r: mean 0
+    hP[OB5 + 1] = 0.f;  // and spread 1
     Model tm;
     float *G, *M1, *M2, *LOSS;
     __nv_bfloat16 *H[4], *GA, *GB2, *TA, *TB;
@@ -1036,6 +1142,60 @@ extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, ui
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return cerr(e);
     }
+    // calibration on the held-out rows: kappa_cal is the 99.9% quantile of
+    // |r - r_net| / sigma (at least 3), so that kappa_cal sigma bounds the
+    // network's error on all but about 1e-3 of the band, raised until the
+    // rows answered at rel_tol 1e-4 are all within a quarter of it
+    float *Z, *SIG;
+    if ((rc = B.get(&Z, nho_pad)) || (rc = B.get(&SIG, nho_pad))) return rc;
+    for (int64_t off = 0; off < nho_pad; off += BATCH) {
+        const int64_t rows = (nho_pad - off) < BATCH ? (nho_pad - off) : BATCH;
+        __nv_bfloat16 *hk[3] = {H[1], H[2], H[3]};
+        __nv_bfloat16 *h4 = nullptr;
+        if ((rc = mlp_forward(tm, rows, Xc + (m + off) * SXP, nullptr, nullptr, H[0], hk, nullptr, err, st, &h4)))
+            return rc;
+        sur_head_eval_kernel<<<nblk(rows * 32, 256), 256, 0, st>>>((int)rows, h4, tm.P, Tc + m + off, (float)tstd,
+                                                                  Z + off, SIG + off);
+    }
+    std::vector<float> hz(nho), hs(nho), hwo(nho);
+    e = cudaMemcpyAsync(hz.data(), Z, nho * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), SIG, nho * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hwo.data(), WTc + m, nho * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cerr(e);
+    std::vector<float> zv;
+    for (int64_t i = 0; i < nho; i++)
+        if (hwo[i] > 0.f) zv.push_back(isfinite(hz[i]) ? hz[i] : 1e30f);
+    double acc_frac = 0, acc_err = 0;
+    if (!zv.empty()) {
+        std::vector<float> zs = zv;
+        const size_t k = (size_t)floor(0.999 * (double)(zs.size() - 1));
+        std::nth_element(zs.begin(), zs.begin() + k, zs.end());
+        nrm.kappa_cal = fmaxf(3.f, zs[k]);
+        // and at least large enough that, at rel_tol 1e-4, every held-out row
+        // the network would answer is within a quarter of the tolerance: the
+        // rows in order of sigma, accepted up to the first larger error
+        std::vector<std::pair<float, float>> se;
+        for (int64_t i = 0; i < nho; i++)
+            if (hwo[i] > 0.f) se.push_back({hs[i], isfinite(hz[i]) ? hz[i] * hs[i] : 1e30f});
+        std::sort(se.begin(), se.end());
+        float smax = 0.f;
+        for (const auto &p : se) {
+            if (!(p.second <= 0.25e-4f)) break;
+            smax = p.first;
+        }
+        nrm.kappa_cal = fmaxf(nrm.kappa_cal, smax > 0.f ? 1e-4f / smax : 1e30f);
+        int64_t na = 0, nv = 0;
+        for (int64_t i = 0; i < nho; i++) {
+            if (!(hwo[i] > 0.f)) continue;
+            nv++;
+            if (nrm.kappa_cal * hs[i] <= 1e-4f) {
+                na++;
+                acc_err = fmax(acc_err, (double)hz[i] * hs[i]);
+            }
+        }
+        acc_frac = nv ? (double)na / nv : 0;
+    }
     int herr = 0;
     e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hP.data(), tm.P, NPAR * 4, cudaMemcpyDeviceToHost, st);
@@ -1049,10 +1209,14 @@ extern "C" int tw_surrogate_train(const char *weights_path, int64_t nsamples, ui
     }
     if (stats) {
         stats[0] = (double)n;                       // positions drawn
-        stats[1] = (double)nl;                      // unflagged (labelled) positions
+        stats[1] = (double)nl;                      // positions of the band (labelled)
         stats[2] = (double)m;                       // training rows used
-        stats[3] = loss_n ? loss_sum / loss_n : 0;  // mean NLL over the last epoch
+        stats[3] = loss_n ? loss_sum / loss_n : 0;  // mean NLL (standardised r) over the last epoch
         stats[4] = tstd;                            // spread of the targets
+        stats[5] = (double)nho;                     // held-out rows
+        stats[6] = nrm.kappa_cal;                   // calibrated acceptance factor
+        stats[7] = acc_frac;                        // held-out rows accepted at rel_tol 1e-4
+        stats[8] = acc_err;                         // their largest error in r
     }
     return TW_OK;
 }
@@ -1080,6 +1244,7 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
     const double *in[5] = {s, q, rho, y1, y2};
     for (int k = 0; k < 5; k++)
         if (ptr_kind(in[k]) != kind) return TW_EINVAL;
+    if (o.pos_status && ptr_kind(o.pos_status) != kind) return TW_EINVAL;
     int devno = 0;
     if (cudaGetDevice(&devno) != cudaSuccess || devno < 0 || devno >= 64) { (void)cudaGetLastError(); return TW_ECUDA; }
     Model *m = nullptr;
@@ -1090,6 +1255,7 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
     T.valid = false;
     const double *din[5];
     double *dout = out;
+    int8_t *dstat = o.pos_status;
     cudaError_t e;
     if (!dev) {  // host arrays: stage through device memory
         for (int k = 0; k < 5; k++) {
@@ -1099,6 +1265,7 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
             din[k] = d;
         }
         if ((rc = B.get(5, &dout, n))) return rc;
+        if (o.pos_status && (rc = B.get(15, &dstat, n))) return rc;
     } else {
         for (int k = 0; k < 5; k++) din[k] = in[k];
     }
@@ -1138,8 +1305,8 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
         cudaEventRecord(ev[1], st);
         __nv_bfloat16 *h4 = nullptr;
         if ((rc = mlp_forward(*m, rows, X, HA, HB, nullptr, nullptr, nullptr, err, st, &h4, ev[2], ev[3]))) return rc;
-        sur_head_infer_kernel<<<nblk(cn * 32, 256), 256, 0, st>>>(cn, c0, h4, m->P, MUPS, FLAG, HEXE, rel_tol,
-                                                                 (float)kappa, dout, LIST, NL);
+        sur_head_infer_kernel<<<nblk(cn * 32, 256), 256, 0, st>>>(cn, c0, h4, m->P, X, m->nrm, MUPS, FLAG, HEXE,
+                                                                 rel_tol, (float)kappa, dout, dstat, LIST, NL);
         cudaEventRecord(ev[4], st);
     }
     unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -1167,10 +1334,12 @@ extern "C" int tw_surrogate_mag(const char *weights_path, const double *s, const
     const unsigned long long nl = cnt[0];
     // contour-integration fallback: one persistent launch over the list
     rc = contour_positions(din[0], din[1], din[2], din[3], din[4], LIST, (int64_t)nl, rel_tol, o.precision,
-                           o.max_samples, dout, nullptr, st);
+                           o.max_samples, dout, dstat, st);
     if (rc) return rc;
     if (!dev) {
         if ((e = cudaMemcpyAsync(out, dout, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cerr(e);
+        if (o.pos_status && (e = cudaMemcpyAsync(o.pos_status, dstat, n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cerr(e);
     }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cerr(e);
     if (counts) {
@@ -1253,6 +1422,7 @@ extern "C" int tw_mag_gated(const double *s, const double *q, const double *rho,
     const double *in[5] = {s, q, rho, y1, y2};
     for (int k = 0; k < 5; k++)
         if (ptr_kind(in[k]) != kind) return TW_EINVAL;
+    if (o.pos_status && ptr_kind(o.pos_status) != kind) return TW_EINVAL;
     int devno = 0;
     if (cudaGetDevice(&devno) != cudaSuccess || devno < 0 || devno >= 64) { (void)cudaGetLastError(); return TW_ECUDA; }
     Pool &B = g_gate_pool[devno];

@@ -16,6 +16,7 @@ Files (text, one position per line: inputs, mu, oracle status):
                           points (one per curve) whose limb passes within rho of the caustic
   paper_worked.txt        the paper's worked configurations (Fig. 1, 2, 5)
   surrogate_queries.txt   1024 positions near the caustics of 64 lenses of the surrogate's range
+  surrogate_band.txt      2048 positions 4-12 rho off the caustics of 64 lenses of the surrogate's range
   central_wide.txt        4096 centres on the central caustic of a wide planetary lens
   lightcurve_orbital.txt  200 points of a central-caustic light curve of an orbiting lens (separation
                           and axis angle linear in time)
@@ -229,6 +230,46 @@ def surrogate_queries():
     _write("surrogate_queries.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
 
 
+def surrogate_band():
+    """Query positions a few source radii off the caustic, where the source
+    does not touch the caustic but its point-source expansion is uncertain
+    (the network's band): 64 lenses of the surrogate's range (seed 405); for
+    each, 32 positions = a random point of a random branch of the oracle's
+    caustic + a displacement of 4-12 rho in a random direction."""
+    rng = np.random.default_rng(405)
+    rows = []
+    jobs = []
+    for k in range(64):
+        s = 10 ** rng.uniform(-0.5, 0.5)
+        q = 10 ** rng.uniform(-5, -1)
+        rho = 10 ** rng.uniform(-4, -2)
+        _, cc = O.caustic(s, q, 256)
+        pts = []
+        for _ in range(32):
+            c = cc[rng.integers(256), rng.integers(4)]
+            r = rho * rng.uniform(4.0, 12.0)
+            a = rng.uniform(0, 2 * np.pi)
+            pts.append((c.real + r * np.cos(a), c.imag + r * np.sin(a)))
+        jobs.append((s, q, rho, np.array(pts)))
+
+    def run(job):
+        s, q, rho, pts = job
+        mu, st, nx = O.mag(s, q, rho, pts[:, 0], pts[:, 1], scan_K=256, nthreads=1)
+        return [(s, q, rho, p[0], p[1], m, a, b) for p, m, a, b in zip(pts, mu, st, nx)]
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
+        for r in ex.map(run, jobs):
+            rows.extend(r)
+    # positions the oracle itself reports as not converged are left out (a cusp
+    # tip reaching just inside the limb between the oracle's caustic samples)
+    nbad = sum(int(r[6]) != 0 for r in rows)
+    rows = [r for r in rows if int(r[6]) == 0]
+    hdr = ("Surrogate band queries: 64 lenses (seed 405) x 32 positions 4-12 rho from a random point of the oracle's\n"
+           "caustic (random branch and angle, random direction); oracle magnifications; %d positions with a\n"
+           "non-zero oracle status left out." % nbad)
+    _write("surrogate_band.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
+
+
 def central_wide():
     """All 4096 positions of the central-caustic set (wide planetary lens,
     source radius comparable to the caustic)."""
@@ -339,6 +380,7 @@ def fig6_sweep():
 
 
 ALL = {"lightcurve_central": lightcurve_central, "central_wide": central_wide, "surrogate_queries": surrogate_queries,
+       "surrogate_band": surrogate_band,
        "map_planetary": map_planetary, "stress_resonant": stress_resonant, "batch_lightcurves": batch_lightcurves,
        "paper_worked": paper_worked, "stress_resonant_1e4": stress_resonant_1e4, "fig4_maps": fig4_maps, "lightcurve_orbital": lightcurve_orbital,
        "limb_darkened": limb_darkened,
