@@ -136,7 +136,8 @@ def config_of(wl, mode, n_gpus):
 
 KERNEL_SOURCES = ("cx.cuh", "lens.cuh", "contour.cuh", "kernels.cuh", "k_fp64_spl1.cu", "k_fp64_spl2.cu",
                   "k_fp64_spl4.cu", "k_mixed_spl1.cu", "k_mixed_spl2.cu", "k_mixed_spl4.cu", "k_fp64_spl2_o4.cu",
-                  "k_mixed_spl2_o4.cu", "k_fp64_repair.cu", "k_mixed_repair.cu")
+                  "k_mixed_spl2_o4.cu", "k_fp64_repair.cu", "k_mixed_repair.cu", "k_fp64_w2.cu", "k_fp64_w4.cu",
+                  "k_mixed_w2.cu", "k_mixed_w4.cu")
 
 
 def sources_sha():
