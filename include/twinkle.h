@@ -140,9 +140,13 @@ int tw_mag_ex(double s, double q, double rho, const double *y1, const double *y2
  * writes the image flux, integrated by parts over the radius, as
  *   mu = [(1 - u) mu_1(rho) + u Int_0^{pi/2} sin^3(phi) mu_1(rho sin phi) dphi] / (1 - u/3),
  * mu_1(r) being the uniform-disc magnification of radius r (the contour
- * integral of tw_mag), and evaluates the phi integral adaptively: trapezoids
- * on 9 to 48 radii, bisected where the change of slope shows a kink (a
- * circle touching the caustic), each uniform disc to rel_tol/2 and the
+ * integral of tw_mag).  mu_1 has kinks at the radii where the circle about
+ * the source centre touches a fold of the caustic or passes over a cusp (the
+ * stationary points of the distance from the centre along the caustic,
+ * found by a sweep of the critical curve); the phi integral is cut there,
+ * each piece mapped by a substitution that is flat at its cut ends, and
+ * integrated by adaptive Simpson panels (error |S - S_halves| / 15 per
+ * panel, up to 40 panels), each uniform disc to rel_tol/2 and the
  * quadrature to rel_tol/2.  One warp per source; opts->err_out receives the
  * summed error estimate, nsamp_out the limb samples of all radii.  Crossings
  * that fail the slope test are reported (TW_POS_SLOPE) and not repaired.
