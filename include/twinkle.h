@@ -256,7 +256,7 @@ int tw_surrogate_train(const char *weights_path, int64_t nsamples, uint64_t seed
  * (arrays s, q, rho, y1, y2; host or device, all of one kind).  A query is
  * flagged as near a caustic when the caustic, swept at 64 angles, comes
  * within 4 rho of the centre, the image count differs between the centre and
- * a ring point, min |J| < 0.1 at the centre, or the expansion's error
+ * a ring point, min |J| < 0.01 at the centre, or the expansion's error
  * estimate exceeds 5% of the value.  An unflagged query is answered without
  * contour integration by the expansion (mu = A_hex) when its error estimate
  * (the gap between its values from the rings (rho/2, rho) and (rho, 2 rho),

@@ -330,6 +330,19 @@ static __device__ __noinline__ int compute_edge(const Arena &ar, int sa, int sb,
     double dEd = (double)dE;
     // a sample that failed the image-count check: keep refining around it
     if ((ma | mb) >> 31) dEd += fabs(dA);
+    // Two three-image samples whose ghost pairs put the caustic within reach
+    // of the limb between them: a pair of crossings closer than the sample
+    // spacing (a five-image stretch no sample has seen) would leave the error
+    // terms smooth and the area short by that stretch.  Each sample's
+    // distance to the caustic (classify_store, in units of rho) bounds where
+    // the caustic can be; the edge is refined like an image-count failure
+    // until its length is below half their sum (no crossing fits between) or
+    // a crossing is sampled.  Samples re-judged by the slope repair carry no
+    // distance and are skipped.
+    if (na == 3 && nb == 3 && !((ma | mb) >> 30)) {
+        const int ga = __ffs(~real_mask(ma) & 31u) - 1, gb = __ffs(~real_mask(mb) & 31u) - 1;
+        if (dthf > 0.5f * (ar.w[sa * 5 + ga] + ar.w[sb * 5 + gb])) dEd += fabs(dA);
+    }
     *outA = dA;
     *outE = dEd;
     return flags;

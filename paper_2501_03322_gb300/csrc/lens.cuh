@@ -408,6 +408,7 @@ __device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, 
     const float rho2 = (float)(L.rho * L.rho);
     uint32_t meta = (uint32_t)count;
     int kp = 0, kn = (count - 1) / 2;
+    float fpp = 0.f;  // mean |f''| of the two ghost roots (three-image samples)
 #pragma unroll 1
     for (int i = 0; i < 5; i++) {
         float Ji = Jf[i];
@@ -421,6 +422,7 @@ __device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, 
         out.roots[i] = z[i];
         out.zp[i] = zp;
         out.w[i] = (rho2 + t.y) * rJ;
+        if (rank[i] >= 3) fpp += 0.5f * sqrtf(norm2(f2));
         if (rank[i] < count) {
             if (Jpos[i] && kp < (count - 1) / 2) { meta |= (uint32_t)i << (3 + 3 * kp); kp++; }
             else if (!Jpos[i] && kn < count) { meta |= (uint32_t)i << (3 + 3 * kn); kn++; }
@@ -436,6 +438,21 @@ __device__ __forceinline__ int classify_store(const LensK &L, cxd y, cxd dzeta, 
 #pragma unroll
             for (int i = 0; i < 5; i++)
                 if (rank[i] == r && r < count) { meta |= (uint32_t)i << (3 + 3 * k); k++; }
+    }
+    // Distance from the limb point to the caustic, estimated from the ghost
+    // pair of a three-image sample: next to a fold the pair that turns real
+    // inside sits at zc +- e with |zeta - zeta_c| = |f''(zc)| |e|^2 / 2, and
+    // the ghost pair outside has the same separation at the same distance
+    // (the geometry of the slope test, Sec. 2.4.2), so the distance is
+    // |f''| |z_g1 - z_g2|^2 / 8.  Stored, in units of rho, in the unused
+    // z' ^ z'' slot of the lower-indexed ghost root (see compute_edge).
+    if (count == 3 && !(flags & SF_IMAGECOUNT)) {
+        int g1 = -1, g2 = -1;
+#pragma unroll
+        for (int i = 0; i < 5; i++)
+            if (rank[i] >= 3) { if (g1 < 0) g1 = i; else g2 = i; }
+        const cxf dg = to_f(z[g1] - z[g2]);
+        out.w[g1] = 0.125f * fpp * norm2(dg) / (float)L.rho;
     }
     *out.meta = meta;
     *out.theta = theta;
