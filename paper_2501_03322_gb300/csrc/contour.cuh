@@ -304,7 +304,8 @@ __device__ __forceinline__ void link_edge(const Arena &ar, int sa, int sb, uint3
     else edge_links<5, 3>(ZA, ZB, links, nlinks, lp, ln);
 }
 
-static __device__ __noinline__ int compute_edge(const Arena &ar, int sa, int sb, double dth, double *outA, double *outE) {
+static __device__ __noinline__ int compute_edge(const Arena &ar, int sa, int sb, double dth, double *outA, double *outE,
+                                                bool guard) {
     const uint32_t ma = ar.meta[sa], mb = ar.meta[sb];
     const int na = meta_count(ma), nb = meta_count(mb);
     uint64_t links;
@@ -330,18 +331,25 @@ static __device__ __noinline__ int compute_edge(const Arena &ar, int sa, int sb,
     double dEd = (double)dE;
     // a sample that failed the image-count check: keep refining around it
     if ((ma | mb) >> 31) dEd += fabs(dA);
-    // Two three-image samples whose ghost pairs put the caustic within reach
-    // of the limb between them: a pair of crossings closer than the sample
-    // spacing (a five-image stretch no sample has seen) would leave the error
-    // terms smooth and the area short by that stretch.  Each sample's
-    // distance to the caustic (classify_store, in units of rho) bounds where
-    // the caustic can be; the edge is refined like an image-count failure
-    // until its length is below half their sum (no crossing fits between) or
-    // a crossing is sampled.  Samples re-judged by the slope repair carry no
-    // distance and are skipped.
-    if (na == 3 && nb == 3 && !((ma | mb) >> 30)) {
+    // Two three-image samples with the caustic close to one of them: a pair
+    // of crossings closer than the sample spacing (a five-image stretch no
+    // sample has seen) would leave the error terms smooth and the area short
+    // by that stretch.  A crossing inside the edge lies within half the edge
+    // of the nearer sample, so that sample's distance to the caustic
+    // (classify_store, in units of rho) is at most half the edge; its
+    // estimate is within a factor 2 there (measured against the oracle's
+    // caustic; a sample farther away, next to a cusp, was overestimated up
+    // to 150x, so the smaller of the two is used).  The edge is refined like an image-count
+    // failure while it is longer than half that smaller distance, until a
+    // crossing is sampled or the caustic is shown to stay away.  Samples
+    // re-judged by the slope repair carry no distance and are skipped.  The
+    // caller turns the guard off once the limb shows a crossing: next to a
+    // sampled crossing the outer edge would otherwise be refined again every
+    // time the crossing edge is (the nearer sample's distance shrinking with
+    // it), and the narrow dip it looks for is the case with no crossing seen.
+    if (guard && na == 3 && nb == 3 && !((ma | mb) >> 30)) {
         const int ga = __ffs(~real_mask(ma) & 31u) - 1, gb = __ffs(~real_mask(mb) & 31u) - 1;
-        if (dthf > 0.5f * (ar.w[sa * 5 + ga] + ar.w[sb * 5 + gb])) dEd += fabs(dA);
+        if (dthf > 0.5f * fminf(ar.w[sa * 5 + ga], ar.w[sb * 5 + gb])) dEd += fabs(dA);
     }
     *outA = dA;
     *outE = dEd;
@@ -433,7 +441,7 @@ static __device__ __noinline__ int slope_fix(const Arena &ar, const uint16_t *or
         const int ee = ((e % N) + N) % N;
         const int s0 = ord[ee], s1 = ord[(ee + 1) % N];
         const double t1 = (ee + 1 < N) ? ar.theta[s1] : ar.theta[s1] + twopi;
-        compute_edge(ar, s0, s1, t1 - ar.theta[s0], &ar.eA[s0], &ar.eE[s0]);
+        compute_edge(ar, s0, s1, t1 - ar.theta[s0], &ar.eA[s0], &ar.eE[s0], false);
     }
     return flags;
 }
@@ -657,7 +665,7 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
 #pragma unroll
     for (int t = 0; t < SPL; t++) {
         const int k = gl * SPL + t;
-        const int ef = compute_edge(ar, k, (k + 1 == SPI) ? 0 : k + 1, twopi / SPI, &ar.eA[k], &ar.eE[k]);
+        const int ef = compute_edge(ar, k, (k + 1 == SPI) ? 0 : k + 1, twopi / SPI, &ar.eA[k], &ar.eE[k], true);
         if (ef & PS_SLOPE) vpos = k;
         xe = xe || (ef & EDGE_XING);
         wc.edges++;
@@ -856,14 +864,14 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
                 const int nx = (P + 1 < N) ? P + 1 : 0;
                 const int sb = ordA[nx];
                 const double tb = (P + 1 < N) ? ar.theta[sb] : twopi;
-                int ef = compute_edge(ar, sl, sb, tb - tn[t], &ar.eA[sl], &ar.eE[sl]);
+                int ef = compute_edge(ar, sl, sb, tb - tn[t], &ar.eA[sl], &ar.eE[sl], !xing);
                 if (ef & PS_SLOPE) vpos = P;
                 xe = xe || (ef & EDGE_XING);
                 wc.edges++;
                 const bool first = (rk[t] == 0) || (ws.pos_new[rk[t] - 1] != tp[t]);
                 if (first) {
                     const int so = ordA[P - 1];
-                    ef = compute_edge(ar, so, sl, tn[t] - ar.theta[so], &ar.eA[so], &ar.eE[so]);
+                    ef = compute_edge(ar, so, sl, tn[t] - ar.theta[so], &ar.eA[so], &ar.eE[so], !xing);
                     if (ef & PS_SLOPE) vpos = P - 1;
                     xe = xe || (ef & EDGE_XING);
                     wc.edges++;

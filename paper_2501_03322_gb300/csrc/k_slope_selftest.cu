@@ -41,7 +41,7 @@ __device__ double edge_at(const Arena &ar, const double *theta, int n, int p, in
     const double twopi = 6.283185307179586476925287;
     const int a = ((p % n) + n) % n, b = (a + 1) % n;
     const double tb = b == 0 ? theta[0] + twopi : theta[b];
-    viol = compute_edge(ar, a, b, tb - theta[a], &ar.eA[a], &ar.eE[a]) & PS_SLOPE;
+    viol = compute_edge(ar, a, b, tb - theta[a], &ar.eA[a], &ar.eE[a], false) & PS_SLOPE;
     return ar.eA[a];
 }
 

@@ -17,6 +17,7 @@ Files (text, one position per line: inputs, mu, oracle status):
   paper_worked.txt        the paper's worked configurations (Fig. 1, 2, 5)
   surrogate_queries.txt   1024 positions near the caustics of 64 lenses of the surrogate's range
   surrogate_band.txt      2048 positions 4-12 rho off the caustics of 64 lenses of the surrogate's range
+  narrow_crossings.txt    limbs that dip into a caustic fold over less than the initial sample spacing
   central_wide.txt        4096 centres on the central caustic of a wide planetary lens
   lightcurve_orbital.txt  200 points of a central-caustic light curve of an orbiting lens (separation
                           and axis angle linear in time)
@@ -270,6 +271,58 @@ def surrogate_band():
     _write("surrogate_band.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
 
 
+def narrow_crossings():
+    """Limbs that dip into the caustic over less than the initial sample
+    spacing: 48 lenses of the surrogate's range (seed 406); for each, a random
+    fold point c of the oracle's caustic with outward normal n (the side with
+    three images), the source centre at c + rho cos(w/2) n with w ~ U[0.02,
+    0.09] rad, so that the limb crosses the fold twice about w apart (2 pi/64 =
+    0.098).  Kept when the oracle finds exactly two crossings less than 0.098
+    apart and converges."""
+    rng = np.random.default_rng(406)
+    rows = []
+    jobs = []
+    for k in range(48):
+        s = 10 ** rng.uniform(-0.5, 0.5)
+        q = 10 ** rng.uniform(-5, -1)
+        rho = 10 ** rng.uniform(-4, -2)
+        _, cc = O.caustic(s, q, 1024)
+        for _ in range(64):  # a fold point: neighbouring chords nearly parallel, the caustic locally straight
+            b = rng.integers(4)
+            i = int(rng.integers(1024))
+            c, t1, t2 = cc[i, b], cc[(i + 1) % 1024, b] - cc[i, b], cc[i, b] - cc[i - 1, b]
+            if abs(t1) == 0 or abs(t2) == 0 or abs(np.angle(t1 / t2)) > 0.02:
+                continue
+            n = 1j * t1 / abs(t1)
+            eps = 1e-3 * rho
+            c_out = O.images(s, q, c + eps * n)["count"], O.images(s, q, c - eps * n)["count"]
+            if c_out == (5, 3):
+                n = -n
+            elif c_out != (3, 5):
+                continue
+            w = rng.uniform(0.02, 0.09)
+            z0 = c + rho * np.cos(0.5 * w) * n
+            jobs.append((s, q, rho, z0.real, z0.imag))
+            break
+
+    def run(job):
+        s, q, rho, y1, y2 = job
+        mu, st, nx = O.mag(s, q, rho, [y1], [y2], scan_K=1024, nthreads=1)
+        xs = O.crossings(s, q, rho, y1, y2, "caustic", 4096)
+        gap = (xs[1] - xs[0]) if len(xs) == 2 else 9.0
+        gap = min(gap, 2 * np.pi - gap)
+        return (s, q, rho, y1, y2, mu[0], st[0], nx[0], gap)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count()) as ex:
+        for r in ex.map(run, jobs):
+            if r[6] == 0 and r[7] == 2 and r[8] < 0.098:
+                rows.append(r[:8])
+    hdr = ("Narrow crossings: 48 lenses (seed 406), the source centre rho cos(w/2) outside a fold point of the\n"
+           "oracle's caustic, w ~ U[0.02, 0.09] rad; kept when the oracle finds two crossings < 0.098 rad apart\n"
+           "(the initial sample spacing 2 pi/64) and converges; oracle magnifications.")
+    _write("narrow_crossings.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
+
+
 def central_wide():
     """All 4096 positions of the central-caustic set (wide planetary lens,
     source radius comparable to the caustic)."""
@@ -380,7 +433,7 @@ def fig6_sweep():
 
 
 ALL = {"lightcurve_central": lightcurve_central, "central_wide": central_wide, "surrogate_queries": surrogate_queries,
-       "surrogate_band": surrogate_band,
+       "surrogate_band": surrogate_band, "narrow_crossings": narrow_crossings,
        "map_planetary": map_planetary, "stress_resonant": stress_resonant, "batch_lightcurves": batch_lightcurves,
        "paper_worked": paper_worked, "stress_resonant_1e4": stress_resonant_1e4, "fig4_maps": fig4_maps, "lightcurve_orbital": lightcurve_orbital,
        "limb_darkened": limb_darkened,
