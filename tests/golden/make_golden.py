@@ -18,6 +18,7 @@ Files (text, one position per line: inputs, mu, oracle status):
   surrogate_queries.txt   1024 positions near the caustics of 64 lenses of the surrogate's range
   surrogate_band.txt      2048 positions 4-12 rho off the caustics of 64 lenses of the surrogate's range
   narrow_crossings.txt    limbs that dip into a caustic fold over less than the initial sample spacing
+  narrow_exits.txt        limbs that leave a caustic over less than the initial sample spacing
   central_wide.txt        4096 centres on the central caustic of a wide planetary lens
   lightcurve_orbital.txt  200 points of a central-caustic light curve of an orbiting lens (separation
                           and axis angle linear in time)
@@ -271,15 +272,14 @@ def surrogate_band():
     _write("surrogate_band.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
 
 
-def narrow_crossings():
-    """Limbs that dip into the caustic over less than the initial sample
-    spacing: 48 lenses of the surrogate's range (seed 406); for each, a random
-    fold point c of the oracle's caustic with outward normal n (the side with
-    three images), the source centre at c + rho cos(w/2) n with w ~ U[0.02,
-    0.09] rad, so that the limb crosses the fold twice about w apart (2 pi/64 =
-    0.098).  Kept when the oracle finds exactly two crossings less than 0.098
-    apart and converges."""
-    rng = np.random.default_rng(406)
+def _narrow(seed, side, name, title):
+    """48 lenses of the surrogate's range; for each, a random fold point c of
+    the oracle's caustic with normal n pointing to the three-image side
+    (side = +1) or the five-image side (side = -1), the source centre at
+    c + rho cos(w/2) n with w ~ U[0.02, 0.09] rad, so that the limb crosses
+    the fold twice about w apart (2 pi/64 = 0.098).  Kept when the oracle
+    finds exactly two crossings less than 0.098 apart and converges."""
+    rng = np.random.default_rng(seed)
     rows = []
     jobs = []
     for k in range(48):
@@ -301,7 +301,7 @@ def narrow_crossings():
             elif c_out != (3, 5):
                 continue
             w = rng.uniform(0.02, 0.09)
-            z0 = c + rho * np.cos(0.5 * w) * n
+            z0 = c + side * rho * np.cos(0.5 * w) * n
             jobs.append((s, q, rho, z0.real, z0.imag))
             break
 
@@ -317,10 +317,23 @@ def narrow_crossings():
         for r in ex.map(run, jobs):
             if r[6] == 0 and r[7] == 2 and r[8] < 0.098:
                 rows.append(r[:8])
-    hdr = ("Narrow crossings: 48 lenses (seed 406), the source centre rho cos(w/2) outside a fold point of the\n"
+    hdr = (title + ": 48 lenses (seed %d), the source centre rho cos(w/2) %s a fold point of the\n"
            "oracle's caustic, w ~ U[0.02, 0.09] rad; kept when the oracle finds two crossings < 0.098 rad apart\n"
-           "(the initial sample spacing 2 pi/64) and converges; oracle magnifications.")
-    _write("narrow_crossings.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
+           "(the initial sample spacing 2 pi/64) and converges; oracle magnifications."
+           % (seed, "outside" if side > 0 else "inside"))
+    _write(name, hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
+
+
+def narrow_crossings():
+    """Limbs that dip into the caustic over less than the initial sample
+    spacing (seed 406, centres on the three-image side)."""
+    _narrow(406, 1.0, "narrow_crossings.txt", "Narrow crossings")
+
+
+def narrow_exits():
+    """Limbs that leave the caustic over less than the initial sample spacing
+    (seed 407, centres on the five-image side)."""
+    _narrow(407, -1.0, "narrow_exits.txt", "Narrow exits")
 
 
 def central_wide():
@@ -433,7 +446,7 @@ def fig6_sweep():
 
 
 ALL = {"lightcurve_central": lightcurve_central, "central_wide": central_wide, "surrogate_queries": surrogate_queries,
-       "surrogate_band": surrogate_band, "narrow_crossings": narrow_crossings,
+       "surrogate_band": surrogate_band, "narrow_crossings": narrow_crossings, "narrow_exits": narrow_exits,
        "map_planetary": map_planetary, "stress_resonant": stress_resonant, "batch_lightcurves": batch_lightcurves,
        "paper_worked": paper_worked, "stress_resonant_1e4": stress_resonant_1e4, "fig4_maps": fig4_maps, "lightcurve_orbital": lightcurve_orbital,
        "limb_darkened": limb_darkened,

@@ -38,7 +38,8 @@ def test_map_rows():
     assert np.allclose(mu, [float(r[3]) for r in rows], rtol=RTOL, atol=0)
 
 
-@pytest.mark.parametrize("name", ["surrogate_queries.txt", "surrogate_band.txt", "narrow_crossings.txt"])
+@pytest.mark.parametrize("name", ["surrogate_queries.txt", "surrogate_band.txt", "narrow_crossings.txt",
+                                  "narrow_exits.txt"])
 def test_per_position_rows(name):
     for r in load(name)[:2]:
         s, q, rho, y1, y2, ref = map(float, r[:6])
@@ -61,7 +62,8 @@ FILES = [("lightcurve_central.txt", 2, 3, 64), ("map_planetary.txt", 4, 5, 64), 
          ("stress_resonant.txt", 4, 5, 0), ("stress_resonant_1e4.txt", 4, 5, 0), ("surrogate_queries.txt", 6, 7, 0),
          ("central_wide.txt", 4, 5, 0), ("paper_worked.txt", 7, 8, 0), ("lightcurve_orbital.txt", 2, 3, 16),
          ("fig4_maps.txt", 5, 6, 64), ("fig6_sweep.txt", 7, 8, 0), ("limb_darkened.txt", 8, 9, 16),
-         ("surrogate_band.txt", 6, 7, 0), ("narrow_crossings.txt", 6, 7, 16)]
+         ("surrogate_band.txt", 6, 7, 0), ("narrow_crossings.txt", 6, 7, 16),
+         ("narrow_exits.txt", 6, 7, 12)]
 
 
 @pytest.mark.parametrize("name,scol,xcol,nx", FILES)

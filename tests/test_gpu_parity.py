@@ -467,16 +467,19 @@ def test_limb_darkened_sources(prec):
         assert rel_err(m0, m1).max() <= 2 * TOL
 
 
+@pytest.mark.parametrize("name", ["narrow_crossings.txt", "narrow_exits.txt"])
 @pytest.mark.parametrize("prec", MODES)
-def test_narrow_crossings_are_sampled(prec):
-    """Limbs that dip into a caustic fold over less than the initial sample
-    spacing (two crossings 0.02-0.09 rad apart against 2 pi/64): no initial
-    sample sees five images, so only the ghost-pair distance guard sends
-    samples there.  Every position against the oracle, per-position lenses
-    (two warps per position) and one lens per call (one warp per position)."""
-    rows = load("narrow_crossings.txt")
+def test_narrow_crossings_are_sampled(prec, name):
+    """Limbs that dip into a caustic fold (or leave it) over less than the
+    initial sample spacing (two crossings 0.02-0.09 rad apart against
+    2 pi/64).  Dipping in, no initial sample sees five images, so only the
+    ghost-pair distance guard sends samples there; leaving, the merging pair
+    of the five-image samples around the gap drives the error terms.  Every
+    position against the oracle, per-position lenses (two warps per
+    position) and one lens per call (one warp per position)."""
+    rows = load(name)
     a = np.array([[float(v) for v in r[:6]] for r in rows])
-    assert len(a) >= 16
+    assert len(a) >= 12
     mu = P.mag_multi(a[:, 0], a[:, 1], a[:, 2], a[:, 3], a[:, 4], rel_tol=TOL, precision=prec)
     assert rel_err(mu, a[:, 5]).max() <= TOL, rel_err(mu, a[:, 5]).max()
     one = np.array([P.mag(r[0], r[1], r[2], r[3:4], r[4:5], rel_tol=TOL, precision=prec)[0] for r in a])
