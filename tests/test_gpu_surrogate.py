@@ -125,3 +125,25 @@ def test_network_answers_match_tight_contour_on_sampled_queries(trained_full):
     ref = P.mag_multi(*sub, rel_tol=1e-7, precision=P.PREC_FP64)
     r = (out[idx] / ref - 1).abs()
     assert r.max().item() <= TOL, r.max().item()
+
+
+def test_full_size_launch_with_oracle_queries(trained_full):
+    """The benchmark's workload at full size: 10^7 queries of its stream
+    (seed 1) in one call, with the 3070 oracle-placed golden queries written
+    over its first entries; those outputs against the oracle, every output
+    finite, the counts adding up."""
+    path, _ = trained_full
+    n = 10_000_000
+    q = P.surrogate_sample(1, n)
+    a1, ok1 = load_queries("surrogate_queries.txt")
+    a2, ok2 = load_queries("surrogate_band.txt")
+    a, ok = np.r_[a1, a2], np.r_[ok1, ok2]
+    m = len(a)
+    for k in range(5):
+        q[k][:m] = torch.as_tensor(a[:, k], device="cuda")
+    out, cnt = P.surrogate_mag(path, *q, rel_tol=TOL, precision=P.PREC_MIXED, details=True)
+    assert cnt["fallback"] + cnt["network"] + cnt["expansion"] == n
+    assert bool(torch.isfinite(out).all())
+    got = out[:m].cpu().numpy()
+    err = np.abs(got[ok] / a[ok, 5] - 1)
+    assert err.max() <= TOL, err.max()
