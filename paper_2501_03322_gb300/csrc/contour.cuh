@@ -544,15 +544,16 @@ struct Coop {
 
 // REPAIR = false: a crossing that fails the slope test only sets PS_SLOPE
 // (the position is then integrated again by the REPAIR = true instance, which
-// repairs such crossings as they appear).  Keeping the repair code out of the
-// main instance keeps its register allocation unchanged.
+// repairs such crossings as they appear; it runs four warps per position, so
+// that the few, long repaired positions use every scheduler of an SM).
+// Keeping the repair code out of the main instance keeps its register
+// allocation unchanged.
 // W warps share the position: 32 W SPL samples per iteration, lane gl = 32 wig
 // + lane of the group taking samples gl SPL .. gl SPL + SPL - 1 of a batch.
 // PosResult.work is this warp's own share.
 template <int PREC, int SPL, bool REPAIR, bool RP = false, int W = 1>
 __device__ PosResult integrate_position(const LensK &L, double tol, int cap, const Arena &ar, WarpStage &ws,
                                         const Coop<W> &co) {
-    static_assert(!REPAIR || W == 1, "the repair pass runs one warp per position");
     static_assert(W == 1 || W == 2 || W == CTA_WARPS, "1, 2 or 4 warps per position");
     static_assert(32 * SPL * W <= 256, "a batch must fit the shared-memory stage");
     constexpr int SPI = 32 * SPL * W;
@@ -677,8 +678,16 @@ __device__ PosResult integrate_position(const LensK &L, double tol, int cap, con
     double A = 0.0, E = 0.0;
     for (;;) {
         // crossings of the last edges that failed the slope test (rare)
-        if (REPAIR) {
+        if (REPAIR && W == 1) {
             if (__any_sync(FULL, vpos >= 0)) flags |= slope_repairs(ar, ordA, N, vpos);
+        } else if (REPAIR) {
+            // a repair re-judges samples and recomputes edges that the other
+            // warps' lanes own: the warps of the group take turns, each turn
+            // closed by a group barrier that every warp passes
+            for (int w = 0; w < W; w++) {
+                if (co.wig == w && __any_sync(FULL, vpos >= 0)) flags |= slope_repairs(ar, ordA, N, vpos);
+                co.sync();
+            }
         } else if (vpos >= 0) {
             flags |= PS_SLOPE;
         }

@@ -1,5 +1,5 @@
 // Kernel instance: mixed-precision root iterations, repair pass of crossings that failed
-// the slope test (two samples per lane).
+// the slope test (four warps per position, one sample per lane).
 #include "kernels.cuh"
 
 namespace tw {

@@ -696,10 +696,10 @@ __global__ void __launch_bounds__(TPB, TW_MIN_CTAS_PER_SM) ld_kernel(KParams kp)
                                                              TPB, 0);                               \
     }
 
-// The repair-pass instance of a precision (two samples per lane).
+// The repair-pass instance of a precision (four warps per position, one sample per lane).
 #define TW_DEFINE_REPAIR_LAUNCHER(PREC)                                                            \
     cudaError_t launch_repair_##PREC(unsigned blocks, cudaStream_t st, const KParams &kp) {       \
-        contour_kernel<PREC, 2, true><<<blocks, TPB, 0, st>>>(kp);                                 \
+        contour_kernel<PREC, 1, true, TW_MIN_CTAS_PER_SM, CTA_WARPS><<<blocks, TPB, 0, st>>>(kp);   \
         return cudaGetLastError();                                                                 \
     }
 

@@ -219,7 +219,7 @@ static int launch(DevState &d, WorkSrc src, double tol, int prec, int max_sample
     auto kernels = [&]() -> cudaError_t {
         cudaError_t e0 = lf((unsigned)blocks, st, kp);
         if (e0 != cudaSuccess) return e0;
-        // at most as many warps as the arena has slots
+        // at most one CTA per SM (one four-warp group and one arena slot each)
         const unsigned rblocks = (unsigned)(blocks < d.nsm ? blocks : d.nsm);
         return (prec == TW_PREC_FP64 ? launch_repair_0 : launch_repair_1)(rblocks, st, kp);
     };
