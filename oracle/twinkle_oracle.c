@@ -789,6 +789,63 @@ static real piece_integral(ctx_t *X, real a, real b, int count, cplx wa, cplx wb
     return A;
 }
 
+/* Area of a limb cut at nx >= 2 crossings xs (ascending angles, each with its
+ * critical point), each piece between consecutive crossings integrated by
+ * piece_integral with the split angles sp[0..nsp-1] that fall inside it.
+ * Sets X->status to ORC_XING unless consecutive pieces alternate between 3
+ * and 5 images. */
+static real pieces_area(ctx_t *X, const xing_t *xs, int nx, const real *sp, int nsp, real tol) {
+    real A = 0;
+    int counts[MAX_XING];
+    for (int i = 0; i < nx; i++) {
+        real a = xs[i].theta;
+        real b = (i + 1 < nx) ? xs[i + 1].theta : xs[0].theta + TWO_PI_L;
+        real mid = 0.5 * (a + b);
+        counts[i] = count_at(X, mid);
+        cplx wa = xs[i].zc, wb = xs[(i + 1) % nx].zc;
+        /* split angles strictly inside the piece */
+        real ins[MAX_SPLIT];
+        int nin = 0;
+        for (int k = 0; k < nsp; k++) {
+            real t = sp[k] < a ? sp[k] + TWO_PI_L : sp[k];
+            if (t > a + 1e-12 * (b - a) && t < b - 1e-12 * (b - a)) ins[nin++] = t;
+        }
+        for (int u = 1; u < nin; u++)
+            for (int k = u; k > 0 && ins[k] < ins[k - 1]; k--) {
+                real t = ins[k]; ins[k] = ins[k - 1]; ins[k - 1] = t;
+            }
+        A += piece_integral(X, a, b, counts[i], wa, wb, ins, nin, tol);
+    }
+    /* consecutive pieces must alternate between 3 and 5 images */
+    for (int i = 0; i < nx; i++) {
+        int c = counts[i], cn = counts[(i + 1) % nx];
+        if (!((c == 3 && cn == 5) || (c == 5 && cn == 3))) X->status = ORC_XING;
+    }
+    return A;
+}
+
+/* Critical point of a crossing at limb angle th found by the image-count
+ * scan: at a fold the two images that merge there sit at zc +- a sqrt(d) +
+ * b d a small angle d inside the five-image side, so their midpoint is zc to
+ * O(d).  Returns 0 when neither side of th shows five images. */
+static int scan_crit_point(ctx_t *X, real th, cplx *zc) {
+    const real d = 1e-16;
+    for (int side = -1; side <= 1; side += 2) {
+        point_t P;
+        cplx zeta = X->zeta0 + X->rho * c_expi(th + side * d);
+        X->nevals++;
+        if (point_solve(&X->L, zeta, &P) != ORC_OK || P.nreal_pair != 5) continue;
+        int bi = 0, bj = 1;
+        real best = c_abs(P.r[0] - P.r[1]);
+        for (int i = 0; i < 5; i++)
+            for (int j = i + 1; j < 5; j++)
+                if (c_abs(P.r[i] - P.r[j]) < best) { best = c_abs(P.r[i] - P.r[j]); bi = i; bj = j; }
+        *zc = 0.5 * (P.r[bi] + P.r[bj]);
+        return 1;
+    }
+    return 0;
+}
+
 static real mag_one(const lens_t *L, const crit_t *C, real y1, real y2, real rho, int scan_K, mag_info_t *info) {
     ctx_t X;
     X.L = *L;
@@ -821,31 +878,7 @@ static real mag_one(const lens_t *L, const crit_t *C, real y1, real y2, real rho
             if (b - a > 1e-30) A += ts_rule(&X, a, b, count, 0, tol / nsp, 40);
         }
     } else {
-        int counts[MAX_XING];
-        for (int i = 0; i < nx; i++) {
-            real a = xs[i].theta;
-            real b = (i + 1 < nx) ? xs[i + 1].theta : xs[0].theta + TWO_PI_L;
-            real mid = 0.5 * (a + b);
-            counts[i] = count_at(&X, mid);
-            cplx wa = xs[i].zc, wb = xs[(i + 1) % nx].zc;
-            /* split angles strictly inside the piece */
-            real ins[MAX_SPLIT];
-            int nin = 0;
-            for (int k = 0; k < nsp; k++) {
-                real t = sp[k] < a ? sp[k] + TWO_PI_L : sp[k];
-                if (t > a + 1e-12 * (b - a) && t < b - 1e-12 * (b - a)) ins[nin++] = t;
-            }
-            for (int u = 1; u < nin; u++)
-                for (int k = u; k > 0 && ins[k] < ins[k - 1]; k--) {
-                    real t = ins[k]; ins[k] = ins[k - 1]; ins[k - 1] = t;
-                }
-            A += piece_integral(&X, a, b, counts[i], wa, wb, ins, nin, tol);
-        }
-        /* consecutive pieces must alternate between 3 and 5 images */
-        for (int i = 0; i < nx; i++) {
-            int c = counts[i], cn = counts[(i + 1) % nx];
-            if (!((c == 3 && cn == 5) || (c == 5 && cn == 3))) X.status = ORC_XING;
-        }
+        A = pieces_area(&X, xs, nx, sp, nsp, tol);
     }
     if (scan_K > 0 && X.status == ORC_OK) {
         real sc[MAX_XING];
@@ -861,6 +894,37 @@ static real mag_one(const lens_t *L, const crit_t *C, real y1, real y2, real rho
             }
             if (!match) X.status = ORC_XING;
         }
+    }
+    /* Crossings the caustic search missed (a cusp tip reaching into the limb
+     * between its caustic samples) leave the quadrature unconverged or the
+     * detectors in disagreement.  The crossings are then the image-count
+     * changes themselves (Sec. 2.3), found by a scan of 4096 limb angles,
+     * each bisected, with critical points from the merging image pairs; the
+     * limb is integrated again on them and the result kept if it converges
+     * with alternating image counts. */
+    if (X.status == ORC_QUAD || X.status == ORC_XING) {
+        ctx_t Y = X;
+        Y.status = ORC_OK;
+        Y.nevals = 0;
+        real sc[MAX_XING];
+        int ns = crossings_scan(&Y, 4096, sc, MAX_XING);
+        if (Y.status == ORC_OK && ns >= 2 && ns % 2 == 0 && ns <= MAX_XING) {
+            xing_t ys[MAX_XING];
+            int ok = 1;
+            for (int i = 0; i < ns && ok; i++) {
+                ys[i].theta = sc[i];
+                ok = scan_crit_point(&Y, sc[i], &ys[i].zc);
+            }
+            if (ok) {
+                real A2 = pieces_area(&Y, ys, ns, sp, nsp, tol);
+                if (Y.status == ORC_OK) {
+                    A = A2;
+                    X.status = ORC_OK;
+                    nx = ns;
+                }
+            }
+        }
+        X.nevals += Y.nevals;
     }
     if (info) {
         info->status = X.status;

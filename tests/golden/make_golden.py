@@ -267,8 +267,8 @@ def surrogate_band():
     nbad = sum(int(r[6]) != 0 for r in rows)
     rows = [r for r in rows if int(r[6]) == 0]
     hdr = ("Surrogate band queries: 64 lenses (seed 405) x 32 positions 4-12 rho from a random point of the oracle's\n"
-           "caustic (random branch and angle, random direction); oracle magnifications; %d positions with a\n"
-           "non-zero oracle status left out." % nbad)
+           "caustic (random branch and angle, random direction); oracle magnifications; positions with a\n"
+           "non-zero oracle status left out: %d." % nbad)
     _write("surrogate_band.txt", hdr, ["s", "q", "rho", "y1", "y2", "mu", "status", "ncross"], rows)
 
 
