@@ -129,7 +129,7 @@ def test_network_answers_match_tight_contour_on_sampled_queries(trained_full):
 
 def test_full_size_launch_with_oracle_queries(trained_full):
     """The benchmark's workload at full size: 10^7 queries of its stream
-    (seed 1) in one call, with the 3070 oracle-placed golden queries written
+    (seed 1) in one call, with the oracle-placed golden queries written
     over its first entries; those outputs against the oracle, every output
     finite, the counts adding up."""
     path, _ = trained_full
